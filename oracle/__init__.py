@@ -1,0 +1,21 @@
+"""Plain float64 CPU oracle for stochastic texture filtering.
+
+TEST INFRASTRUCTURE ONLY.  Nothing on the product path may import, call or link
+this package: only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg
+of ``bench.py`` use it.  It shares no code with the CUDA library.
+
+Modules (each cites the passage of the paper it follows):
+
+* ``philox``   -- counter-based generator for the variates xi (Section 2.2).
+* ``kernels``  -- the 1D filter kernels of Appendix A.
+* ``codecs``   -- binary16 and E4M3 storage formats.
+* ``textures`` -- texel stores: 2D MIP pyramids, dense and sparse 3D grids.
+* ``filters``  -- deterministic (Eq. 2, Eq. 9) and stochastic (Eq. 3, sampling
+  arrays of Section 2.2) lookups, and the exact expectation by enumeration.
+* ``mlp``      -- float64 forward and backward of the neural-texture decoder.
+
+Every function is pinned by a test in ``tests/test_oracle_*.py`` against something
+other than itself (closed forms, brute force, an independent library, or a value
+the paper prints).
+"""
+from . import philox, kernels, codecs, textures, filters  # noqa: F401
