@@ -1,0 +1,389 @@
+#!/usr/bin/env python3
+"""Benchmark: filtered lookups/s, stochastic vs deterministic, on one GB300.
+
+Default workload (the dense-grid configuration): a 256^3 FP16 density grid from
+seeded fractal noise (~30% non-zero) and 1920x1080 rays x 16 ray-march steps
+(33,177,600 queries) from a seeded pinhole camera; B-spline tricubic filtering.
+One step = one stochastic lookup batch over all queries (query ingest, per-axis
+weights, Philox variates, inverse-CDF tap choice, address, single-texel fetch,
+scale and store).  The same-GPU deterministic 64-tap filter, the trilinear pair and
+the Morton-binned variant are timed beside it and reported in extra keys.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+                    [--workload dense|tex2d|sparse]
+
+Timing: CUDA events on the launching stream, W untimed warm-up steps, barrier and
+synchronize on both sides of K timed steps, max over ranks.  The query and output
+arrays (531 MB per step) are larger than L2, so no extra flush is needed; the
+32 MiB grid stays L2-resident by design.  Under torchrun every rank runs the same
+per-rank workload (weak scaling, no data-path collective).
+"""
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+ALGO_BYTES = {  # algorithmic bytes per lookup: query in + texel(s) + result out
+    ("dense", "stochastic"): 12 + 2 + 4,
+    ("dense", "deterministic", "bspline3"): 12 + 64 * 2 + 4,
+    ("dense", "deterministic", "linear"): 12 + 8 * 2 + 4,
+    ("tex2d", "stochastic"): 8 + 16 + 16,
+    ("tex2d", "deterministic", "bspline3"): 8 + 16 * 16 + 16,
+    ("tex2d", "deterministic", "linear"): 8 + 4 * 16 + 16,
+}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="dense", choices=["dense", "tex2d"])
+    ap.add_argument("--filter", default="bspline3", choices=["linear", "bspline3", "catmull_rom"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--quick", action="store_true", help="skip the extra variants")
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------------ workload
+
+def make_workload(name):
+    import synth
+    if name == "dense":
+        vals = synth.dense_density(n=256, seed=3)
+        q = synth.camera_queries(**synth.C2_RAYS)
+        desc = "dense 256^3 FP16 fractal-noise density (30% non-zero), 1920x1080 rays x 16 steps"
+        return dict(name=name, values=vals, coords=q, dims=(256, 256, 256), channels=1, desc=desc)
+    tex = synth.texture2d(256, 256, 4, seed=1)
+    n = 1 << 24
+    uv = synth.uv_queries(n, seed=2)
+    desc = "2D 256x256 RGBA FP32 value noise, 16,777,216 uniform uv queries"
+    return dict(name=name, values=tex, coords=uv, dims=(256, 256, 1), channels=4, desc=desc)
+
+
+def make_texture(stf, w, fmt=None):
+    if w["name"] == "dense":
+        return stf.Texture(stf.KIND_DENSE3D, w["values"], dims=w["dims"],
+                           fmt=stf.FMT_F16 if fmt is None else fmt)
+    return stf.Texture(stf.KIND_TEX2D, w["values"], dims=w["dims"], channels=4)
+
+
+# ------------------------------------------------------------------ clocks
+
+class ClockSampler:
+    """nvidia-smi samples during the timed region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.lines = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, ValueError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ timing
+
+def time_steps(torch, fn, steps, warmup, stream, dist=None):
+    """Per-step CUDA-event durations (ms) of fn() on `stream`, and the total (ms)."""
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
+    ev[0].record(stream)
+    for k in range(steps):
+        fn()
+        ev[k + 1].record(stream)
+    torch.cuda.synchronize()
+    per = [ev[k].elapsed_time(ev[k + 1]) for k in range(steps)]
+    total = ev[0].elapsed_time(ev[steps])
+    if dist is not None:
+        dist.barrier()
+    return per, total
+
+
+def pct(xs, p):
+    xs = sorted(xs)
+    i = min(len(xs) - 1, max(0, int(round(p / 100.0 * (len(xs) - 1)))))
+    return xs[i]
+
+
+def kernel_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2305_05810_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        if f.endswith((".cu", ".cuh", ".h")):
+            h.update(open(os.path.join(csrc, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(key):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on the
+    current kernel sources; else None."""
+    p = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    try:
+        d = json.load(open(p))
+        e = d.get(key)
+        if e and e.get("kernel_hash") == kernel_hash():
+            return e["dram_bytes_per_launch"]
+    except (OSError, ValueError):
+        pass
+    return None
+
+
+def peaks():
+    try:
+        d = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        return float(d["hbm_gbs"]), "measured"
+    except (OSError, ValueError, KeyError):
+        return 6800.0, "fallback"
+
+
+# ------------------------------------------------------------------ CPU oracle
+
+def cpu_oracle_rate(w, filt, n_queries):
+    """Oracle lookups/s on the first n_queries queries (stochastic), chunked."""
+    from oracle import codecs, filters, textures
+    if w["name"] == "dense":
+        ref = textures.Dense3D(codecs.f16_decode(codecs.f16_encode(w["values"].astype(np.float64))))
+    else:
+        ref = textures.Texture2D([w["values"].astype(np.float64)])
+    q = w["coords"][:n_queries]
+    t0 = time.perf_counter()
+    for a in range(0, q.shape[0], 1 << 20):
+        b = min(q.shape[0], a + (1 << 20))
+        qid = np.arange(a, b, dtype=np.uint64)
+        if w["name"] == "dense":
+            filters.lookup_3d(ref, q[a:b], filt, stochastic_form=True, seed=1, qid=qid)
+        else:
+            filters.lookup_2d(ref, q[a:b], None, filt, stochastic_form=True, seed=1, qid=qid)
+    dt = time.perf_counter() - t0
+    return q.shape[0] / dt, dt
+
+
+# ------------------------------------------------------------------ arms
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    w = make_workload(args.workload)
+    n_sample = 1 << 21
+    rates = []
+    for k in range(args.warmup + args.steps):
+        r, _ = cpu_oracle_rate(w, args.filter, n_sample)
+        if k >= args.warmup:
+            rates.append(r)
+    total_time = sum(n_sample / r for r in rates)
+    value = n_sample * len(rates) / total_time
+    line = {
+        "impl": "reference", "metric": "filtered lookups/s (stochastic, %s)" % args.filter,
+        "value": value, "unit": "lookups/s", "n_gpus": args.gpus, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1000 * total_time / len(rates),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": w["desc"], "filter": args.filter,
+                                         "queries_per_step": n_sample},
+        "cpu_baseline": {"value": value, "unit": "lookups/s", "cores": 1, "kind": "oracle",
+                         "sample": "first %d queries of the workload per step" % n_sample},
+        "e2e": {"value": value, "unit": "lookups/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import torch
+    import paper_2305_05810_gb300 as stf
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as tdist
+        torch.cuda.set_device(local)
+        tdist.init_process_group("nccl")
+        dist = tdist
+    dev = torch.device("cuda", torch.cuda.current_device())
+    stf.load()
+
+    w = make_workload(args.workload)
+    tex = make_texture(stf, w)
+    n = w["coords"].shape[0]
+    C = w["channels"]
+    coords = torch.from_numpy(w["coords"]).to(dev)
+    out = torch.empty((n, C), dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+    filt = args.filter
+
+    def stochastic(f=filt, **kw):
+        p = stf.make_params(f, seed=2024, **kw)
+        return lambda: stf.stf_lookup_batch(tex.handle, p, coords, None, n, out, None, stream)
+
+    def deterministic(f):
+        p = stf.make_params(f)
+        return lambda: stf.stf_lookup_batch_deterministic(tex.handle, p, coords, None, n, out, stream)
+
+    gpu_index = torch.cuda.current_device()
+    if os.environ.get("CUDA_VISIBLE_DEVICES"):
+        try:
+            gpu_index = int(os.environ["CUDA_VISIBLE_DEVICES"].split(",")[gpu_index])
+        except ValueError:
+            pass
+    with ClockSampler(gpu_index) as clk:
+        per, total = time_steps(torch, stochastic(), args.steps, args.warmup, stream, dist)
+    stf.stf_synchronize(tex.handle, stream)
+
+    # max over ranks
+    t_total = torch.tensor([total], dtype=torch.float64, device=dev)
+    if dist is not None:
+        dist.all_reduce(t_total, op=dist.ReduceOp.MAX)
+    total = float(t_total.item())
+    value = n * world * args.steps / (total / 1000.0)
+
+    extras = {}
+    if not args.quick:
+        variants = [("deterministic_" + filt, deterministic(filt))]
+        if filt != "linear":
+            variants += [("stochastic_linear", stochastic("linear")),
+                         ("deterministic_linear", deterministic("linear"))]
+        variants += [("stochastic_binned", stochastic(bin_queries=True))]
+        for name, fn in variants:
+            try:
+                p2, t2 = time_steps(torch, fn, max(3, args.steps // 2), 2, stream)
+                extras[name] = {"lookups_per_s": n * len(p2) / (t2 / 1000.0),
+                                "ms_p50": pct(p2, 50), "ms_p99": pct(p2, 99)}
+            except stf.StfError as e:
+                extras[name] = {"unavailable": str(e)}
+        det = extras.get("deterministic_" + filt, {})
+        if "lookups_per_s" in det:
+            extras["speedup_vs_deterministic"] = value / world / det["lookups_per_s"]
+
+    # end to end: pinned host coords -> device, lookup, device -> host each step
+    h_coords = torch.from_numpy(w["coords"]).pin_memory()
+    h_out = torch.empty((n, C), dtype=torch.float32).pin_memory()
+    d_in = torch.empty_like(coords)
+    pe = stf.make_params(filt, seed=2024)
+
+    def e2e_step():
+        d_in.copy_(h_coords, non_blocking=True)
+        stf.stf_lookup_batch(tex.handle, pe, d_in, None, n, out, None, stream)
+        h_out.copy_(out, non_blocking=True)
+
+    pe2, te2 = time_steps(torch, e2e_step, max(3, args.steps // 2), 2, stream, dist)
+    t_e2e = torch.tensor([te2], dtype=torch.float64, device=dev)
+    if dist is not None:
+        dist.all_reduce(t_e2e, op=dist.ReduceOp.MAX)
+    e2e_value = n * world * len(pe2) / (float(t_e2e.item()) / 1000.0)
+
+    if dist is not None:
+        dist.barrier()
+    if rank != 0:
+        dist.destroy_process_group()
+        return 0
+
+    hbm, peak_kind = peaks()
+    algo = ALGO_BYTES[(w["name"], "stochastic")]
+    avg_launch_ms = statistics.mean(per)
+    achieved = algo * n / (avg_launch_ms / 1000.0) / 1e9
+    traffic = ncu_traffic("%s_stochastic_%s" % (w["name"], filt))
+    line = {
+        "metric": "filtered lookups/s (stochastic, %s)" % filt,
+        "value": value, "unit": "lookups/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32 (fp16 texels)" if w["name"] == "dense" else "f32",
+        "data": "synthetic",
+        "config": {"workload": w["desc"], "filter": filt, "queries_per_step": n,
+                   "l2": "inputs larger than L2 (query+output arrays %d MB per step)"
+                         % ((w["coords"].nbytes + n * C * 4) // 10**6),
+                   "parallelism": "replica per GPU" if world > 1 else "single GPU"},
+        "ms_p50": pct(per, 50), "ms_p99": pct(per, 99),
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                     "frac": achieved / hbm, "traffic": traffic,
+                     "algorithmic_bytes_per_lookup": algo, "peak_source": peak_kind},
+        "e2e": {"value": e2e_value, "unit": "lookups/s",
+                "h2d_bytes_per_step": int(w["coords"].nbytes),
+                "d2h_bytes_per_step": int(n * C * 4)},
+        "gpu_launches": args.steps,
+        "clocks": clk.summary(),
+        "extras": extras,
+    }
+    if not args.no_cpu_baseline:
+        rate, dt = cpu_oracle_rate(w, filt, 1 << 23)
+        line["cpu_baseline"] = {"value": rate, "unit": "lookups/s", "cores": 1, "kind": "oracle",
+                                "sample": "first %d queries of the workload, stochastic %s, "
+                                          "%.1f s" % (1 << 23, filt, dt)}
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    tex.close()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

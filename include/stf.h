@@ -1,0 +1,189 @@
+/*
+ * stf.h -- C ABI of the GB300 stochastic texture filtering library (libstf.so).
+ *
+ * The library performs batched filtered lookups into 2D MIP-mapped textures and
+ * dense or sparse 3D voxel grids, following "Stochastic Texture Filtering"
+ * (Fajardo, Wronski, Salvi, Pharr; arXiv 2305.05810):
+ *
+ *   stochastic form   -- one tap per axis is drawn with probability |w| / sum|w|
+ *                        from the separable filter weights (sampling arrays,
+ *                        Section 2.2; Eq. 7-9 in Section 4) and the single texel
+ *                        is returned, times sign(w) * sum|w| per axis for kernels
+ *                        with negative lobes (Section 2.2, "Positivization", first
+ *                        sentence).  Its expectation is the filtered value (Eq. 3).
+ *   deterministic form -- the full weighted sum over 4 / 8 / 16 / 64 taps (Eq. 2,
+ *                        Eq. 9), the same-GPU baseline.
+ *
+ * Conventions shared by every entry point:
+ *   - Every call returns an stf_status.  On failure stf_last_error() returns a
+ *     message for the calling thread.  Argument errors are reported before any
+ *     work is queued.
+ *   - Device pointers ("d_" prefix) are CUDA device (or managed) memory owned by
+ *     the caller; host pointers ("h_" prefix) are ordinary host memory.
+ *   - Work is queued on the given CUDA stream (cudaStream_t passed as void*; NULL
+ *     is the legacy default stream) and is asynchronous unless stated otherwise.
+ *   - n == 0 is a no-op that returns STF_OK.
+ *   - Coordinates: 2D lookups take texture coordinates (u, v); the raster position
+ *     on level L is x = u * W_L - 1/2 (texel centres at i + 1/2).  3D lookups take
+ *     index-space positions; voxel values sit at integer coordinates.  A NaN or
+ *     infinite coordinate (or level of detail) yields the background value.
+ *   - Addressing: 2D clamps to the edge; dense and sparse 3D read the background
+ *     value outside the grid / outside active leaves.
+ *   - Random variates: the i-th query of a call draws its variates from
+ *     Philox4x32-10 with key = seed and counter = (q, q >> 32, sample_index, 0),
+ *     q = query_offset + i.  Results therefore do not depend on how a batch is
+ *     split into calls, on launch shape, or on what else runs on the GPU.
+ */
+#ifndef STF_H_
+#define STF_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct stf_texture_s* stf_texture; /* opaque handle owned by the library */
+
+typedef enum {
+  STF_OK = 0,
+  STF_ERR_INVALID_ARGUMENT = 1, /* bad pointer, size, enum value or descriptor */
+  STF_ERR_INVALID_HANDLE = 2,   /* handle never created or already destroyed */
+  STF_ERR_OUT_OF_MEMORY = 3,    /* a device or host allocation failed */
+  STF_ERR_UNSUPPORTED = 4,      /* valid request this texture kind cannot serve */
+  STF_ERR_CUDA = 5,             /* a CUDA runtime call failed (message has details) */
+  STF_ERR_DEVICE_ASSERT = 6,    /* a kernel found an inconsistent data structure */
+  STF_ERR_BUDGET = 7            /* a memory budget would be exceeded */
+} stf_status;
+
+typedef enum {
+  STF_KIND_TEX2D = 0,    /* 2D texture, optional MIP pyramid */
+  STF_KIND_DENSE3D = 1,  /* dense voxel grid */
+  STF_KIND_SPARSE3D = 2  /* sparse grid: root -> upper (32^3) -> lower (16^3) -> 8^3 leaves */
+} stf_kind;
+
+typedef enum {
+  STF_FMT_F32 = 0,        /* IEEE binary32 texels */
+  STF_FMT_F16 = 1,        /* IEEE binary16 texels (round-to-nearest-even at create) */
+  STF_FMT_E4M3_SCALED = 2 /* sparse only: OCP FP8 E4M3 codes with one float32 scale
+                             per leaf, scale = max|v| / 448 */
+} stf_format;
+
+typedef enum {
+  STF_FILTER_LINEAR = 0,     /* tent kernel K1: bilinear / trilinear (Eq. 7, Eq. 8) */
+  STF_FILTER_BSPLINE3 = 1,   /* cubic B-spline K_bs, 4 taps per axis (Eq. 9) */
+  STF_FILTER_CATMULL_ROM = 2 /* cubic K3 with a = -1/2 (Appendix A), 4 taps per axis */
+} stf_filter;
+
+typedef enum {
+  STF_LEVEL_NEAREST = 0,   /* level floor(lod + 1/2) in both forms */
+  STF_LEVEL_STOCHASTIC = 1 /* stochastic: floor(lod + u); deterministic: blend of
+                              floor(lod) and the next level by frac(lod)
+                              (trilinear MIP mapping, Section 2.1) */
+} stf_level_mode;
+
+/* Texture description for stf_create_texture.
+ *   TEX2D:    dims = {W, H, 1}; channels in {1, 2, 4, 8}; format F32 or F16;
+ *             mip_levels >= 1.  h_data/d_data holds float32 texels
+ *             [level][y][x][channel]; all levels concatenated, level L being
+ *             max(1, W >> L) x max(1, H >> L), unless generate_mips != 0, in which
+ *             case it holds level 0 only and the library builds the other levels
+ *             with a 2x2 box filter (power-of-two W and H required).
+ *   DENSE3D:  dims = {X, Y, Z}; channels 1; format F32 or F16; float32 values
+ *             [z][y][x].
+ *   SPARSE3D: leaf_origins = num_leaves x 3 int32 (x, y, z), each a multiple of 8
+ *             and distinct; data holds num_leaves x 512 float32 values, laid out
+ *             [leaf][x & 7][y & 7][z & 7]; format F32 or E4M3_SCALED; dims ignored.
+ *   data points to host memory if data_on_device == 0, else to device memory.
+ *   The library copies (and quantises) the data; the caller keeps ownership.
+ */
+typedef struct {
+  int32_t kind;           /* stf_kind */
+  int32_t format;         /* stf_format */
+  int32_t dims[3];
+  int32_t channels;
+  int32_t mip_levels;
+  int32_t generate_mips;
+  int32_t data_on_device;
+  int32_t reserved0;
+  const void* data;               /* float32 values, see above */
+  const int32_t* leaf_origins;    /* sparse only; host or device per data_on_device */
+  int64_t num_leaves;             /* sparse only */
+  float background;               /* value outside the grid / in inactive regions */
+  int32_t reserved1;
+} stf_texture_desc;
+
+/* Per-call lookup parameters. */
+typedef struct {
+  int32_t filter;         /* stf_filter */
+  int32_t level_mode;     /* stf_level_mode; used only when d_lod != NULL */
+  uint64_t seed;          /* Philox key */
+  uint64_t query_offset;  /* q of the first query of this call */
+  uint32_t sample_index;  /* third Philox counter word */
+  int32_t bin_queries;    /* 1: counting-sort queries by spatial tile first
+                             (same results, better gather locality) */
+  int32_t reuse_xi;       /* 1: one variate carried across axes by the remapping
+                             of Eq. 4 instead of one variate per axis */
+  int32_t reserved;
+} stf_lookup_params;
+
+/* Create a device-resident texture from desc; queued on `stream`, and the call
+ * synchronises that stream before returning so that the caller may free its data.
+ * Returns STF_ERR_INVALID_ARGUMENT for an inconsistent descriptor,
+ * STF_ERR_OUT_OF_MEMORY if device memory runs out (nothing is leaked). */
+stf_status stf_create_texture(const stf_texture_desc* desc, void* stream, stf_texture* out);
+
+/* Release a texture and everything it owns.  Waits for work queued on it. */
+stf_status stf_destroy(stf_texture tex);
+
+/* Stochastic filtered lookups (one texel per query; Eq. 3 with the sampling-arrays
+ * rule of Section 2.2 applied per axis, Section 4.2).
+ *   d_coords: n x 2 float32 (u, v) for TEX2D, n x 3 float32 (x, y, z) otherwise.
+ *   d_lod:    NULL (level 0) or n float32 levels of detail (log2 footprint in level-0
+ *             texels), TEX2D only.
+ *   d_out:    n x channels float32, query-major.
+ *   d_taps:   NULL or n x 4 int32 receiving the chosen texel (x, y, z, level) before
+ *             clamping; level = -1 when nothing was fetched (non-finite input). */
+stf_status stf_lookup_batch(stf_texture tex, const stf_lookup_params* params,
+                            const float* d_coords, const float* d_lod, int64_t n,
+                            float* d_out, int32_t* d_taps, void* stream);
+
+/* Deterministic filtered lookups: the full 2^d or 4^d tap weighted sum (Eq. 2,
+ * Eq. 9) with float32 accumulation; arguments as for stf_lookup_batch. */
+stf_status stf_lookup_batch_deterministic(stf_texture tex, const stf_lookup_params* params,
+                                          const float* d_coords, const float* d_lod,
+                                          int64_t n, float* d_out, void* stream);
+
+/* Validation accumulators for unbiasedness checks: for each query, n_samples
+ * stochastic lookups with sample_index = params->sample_index + s, summed in
+ * float64.  d_sum and d_sumsq are n x channels float64 (overwritten). */
+stf_status stf_lookup_accumulate(stf_texture tex, const stf_lookup_params* params,
+                                 const float* d_coords, const float* d_lod, int64_t n,
+                                 int32_t n_samples, double* d_sum, double* d_sumsq,
+                                 void* stream);
+
+/* Bytes of device memory the texture holds (texels, tree nodes, scratch). */
+stf_status stf_texture_bytes(stf_texture tex, int64_t* out_bytes);
+
+/* Wait for `stream`, then report and clear the texture's device status word:
+ * STF_ERR_DEVICE_ASSERT if a kernel flagged an inconsistent structure since the
+ * last check, STF_ERR_CUDA if the stream reported an error, else STF_OK. */
+stf_status stf_synchronize(stf_texture tex, void* stream);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char* stf_last_error(void);
+
+/* ABI version (major * 10000 + minor * 100 + patch). */
+int32_t stf_version(void);
+
+/* Failure-injection hook for tests of the error paths: the k-th device allocation
+ * the library makes from now on fails as if the device were out of memory, and the
+ * call that made it returns STF_ERR_OUT_OF_MEMORY with nothing leaked.  k <= 0
+ * disables the hook.  Not thread-safe; meant for single-threaded tests. */
+void stf_debug_fail_allocation(int64_t k);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* STF_H_ */

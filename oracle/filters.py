@@ -142,10 +142,11 @@ def deterministic(fetch, xs32, filt, background=0.0):
     return total
 
 
-def expectation_by_enumeration(fetch, xs32, filt):
-    """E[<F>] = sum over tap combinations of p(combo) * estimate(combo), with
-    p = prod |w| / S and estimate = prod(sign(w) S) * t (or t for non-negative
-    kernels)."""
+def expectation_by_enumeration(fetch, xs32, filt, power=1):
+    """E[<F>^power] = sum over tap combinations of p(combo) * estimate(combo)^power,
+    with p = prod |w| / S and estimate = prod(sign(w) S) * t (or t for non-negative
+    kernels).  power=1 gives the expectation (Eq. 3), power=2 the second moment from
+    which the exact variance of one stochastic lookup follows."""
     offs, _, nonneg = FILTERS[filt]
     frames = [axis_frame(x) for x in xs32]
     weights = [axis_weights(f, filt) for (_, f, _) in frames]
@@ -160,7 +161,7 @@ def expectation_by_enumeration(fetch, xs32, filt):
             if not nonneg:
                 sig = sig * np.sign(wk) * sums[a]
         t = fetch(*[frames[a][0] + offs[combo[a]] for a in range(len(xs32))])
-        term = (p * sig)[:, None] * t
+        term = p[:, None] * (sig[:, None] * t) ** power
         total = term if total is None else total + term
     return total
 

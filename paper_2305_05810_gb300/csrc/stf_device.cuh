@@ -1,0 +1,214 @@
+// Device-side building blocks of the lookup kernels: the counter-based generator,
+// the separable filter weights, the inverse-CDF tap choice and the texture views.
+// Written for sm_103a; every function here is inlined into the kernels.
+#pragma once
+#include <cuda_fp16.h>
+#include <cuda_fp8.h>
+#include <stdint.h>
+
+#include "stf_types.h"
+
+namespace stf {
+
+// ---------------------------------------------------------------- Philox4x32-10
+// Salmon, Moraes, Dror, Shaw, "Parallel random numbers: as easy as 1, 2, 3"
+// (SC'11): ten rounds of two 32x32->64 multiplies; the key is bumped by the Weyl
+// constants between rounds.  The key is a kernel argument, so its schedule is the
+// same for every thread.
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    if (r > 0) {
+      k0 += 0x9E3779B9u;
+      k1 += 0xBB67AE85u;
+    }
+    const uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
+    const uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
+    c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+  }
+  return c;
+}
+
+// Top 24 bits as a float in [0, 1): exact in float32.
+__device__ __forceinline__ float unit24(uint32_t r) { return (float)(r >> 8) * 0x1p-24f; }
+
+// ---------------------------------------------------------------- filter weights
+// Weights of the taps floor(x) + OFF0 + k, k = 0..T-1, at fraction f = x - floor(x).
+template <int F> struct Filter;
+
+// Tent K1 (Appendix A): taps floor(x), floor(x)+1.
+template <> struct Filter<STF_FILTER_LINEAR> {
+  static constexpr int T = 2, OFF0 = 0;
+  static constexpr bool NONNEG = true;
+  __device__ __forceinline__ static void weights(float f, float* w) {
+    w[0] = 1.0f - f;
+    w[1] = f;
+  }
+};
+
+// Cubic B-spline K_bs (Appendix A, "Convolutional"): with g = 1 - f the four taps
+// floor(x)-1 .. floor(x)+2 carry g^3/6, f^2(f/2 - 1) + 2/3, g^2(g/2 - 1) + 2/3, f^3/6.
+template <> struct Filter<STF_FILTER_BSPLINE3> {
+  static constexpr int T = 4, OFF0 = -1;
+  static constexpr bool NONNEG = true;
+  __device__ __forceinline__ static void weights(float f, float* w) {
+    const float g = 1.0f - f;
+    w[0] = g * g * g * (1.0f / 6.0f);
+    w[1] = fmaf(f * f, fmaf(0.5f, f, -1.0f), 2.0f / 3.0f);
+    w[2] = fmaf(g * g, fmaf(0.5f, g, -1.0f), 2.0f / 3.0f);
+    w[3] = f * f * f * (1.0f / 6.0f);
+  }
+};
+
+// Cubic K3 with a = -1/2 (Appendix A), Catmull-Rom: -f g^2 / 2, 1 + f^2(3f/2 - 5/2),
+// 1 + g^2(3g/2 - 5/2), -g f^2 / 2.
+template <> struct Filter<STF_FILTER_CATMULL_ROM> {
+  static constexpr int T = 4, OFF0 = -1;
+  static constexpr bool NONNEG = false;
+  __device__ __forceinline__ static void weights(float f, float* w) {
+    const float g = 1.0f - f;
+    w[0] = -0.5f * f * g * g;
+    w[1] = fmaf(f * f, fmaf(1.5f, f, -2.5f), 1.0f);
+    w[2] = fmaf(g * g, fmaf(1.5f, g, -2.5f), 1.0f);
+    w[3] = -0.5f * g * f * f;
+  }
+};
+
+// ---------------------------------------------------------------- tap choice
+// Smallest k with u*S < C_k, C_k = running float32 sum of |w_j|, S = C_{T-1}
+// (sampling arrays, Section 2.2); if rounding leaves none, the last tap with
+// |w| > 0.  Returns k; S, sign(w_k) and the Eq. 4 remapped variate through the
+// references.
+template <int T>
+__device__ __forceinline__ int choose_tap(float u, const float* w, float& S, float& sgn,
+                                          float& u_next) {
+  float c[T];
+  float acc = 0.0f;
+  int last_nz = 0;
+#pragma unroll
+  for (int k = 0; k < T; ++k) {
+    const float a = fabsf(w[k]);
+    acc = __fadd_rn(acc, a);
+    c[k] = acc;
+    if (a > 0.0f) last_nz = k;
+  }
+  S = acc;
+  const float us = __fmul_rn(u, S);
+  int k = last_nz;
+#pragma unroll
+  for (int j = T - 1; j >= 0; --j)
+    if (us < c[j]) k = j;
+  float cprev = 0.0f, wk = 0.0f;
+  sgn = 1.0f;
+#pragma unroll
+  for (int j = 0; j < T; ++j) {
+    if (j == k) {
+      wk = fabsf(w[j]);
+      sgn = w[j] < 0.0f ? -1.0f : 1.0f;
+    }
+    if (j + 1 == k) cprev = c[j];
+  }
+  u_next = fminf(fmaxf(__fdiv_rn(__fsub_rn(us, cprev), wk), 0.0f), 0x1.fffffep-1f);
+  return k;
+}
+
+// Integer tap base floor(x) (clamped to +-2^24) and fraction x - floor(x).
+__device__ __forceinline__ int axis_base(float x, float& f) {
+  const float fl = floorf(x);
+  f = __fsub_rn(x, fl);
+  return (int)fminf(fmaxf(fl, -16777216.0f), 16777216.0f);
+}
+
+// ---------------------------------------------------------------- views
+struct Tex2DView {
+  const void* texels;     // storage format, [level][y][x][c]
+  int64_t level_off[STF_MAX_LEVELS];   // element offset (in texels) of each level
+  int32_t level_w[STF_MAX_LEVELS];
+  int32_t level_h[STF_MAX_LEVELS];
+  int32_t levels;
+};
+
+struct Dense3DView {
+  const void* texels;     // [z][y][x]
+  int32_t nx, ny, nz;
+  float background;
+};
+
+struct LookupArgs {
+  const float* coords;
+  const float* lod;
+  int64_t n;
+  float* out;
+  int32_t* taps;
+  uint32_t key0, key1;
+  uint64_t query_offset;
+  uint32_t sample_index;
+  int32_t reuse;
+  int32_t level_mode;
+  int32_t n_samples;      // accumulate kernels
+  double* sum;
+  double* sumsq;
+};
+
+template <int FMT, int C> struct TexelIO;
+
+template <int C> struct TexelIO<STF_FMT_F32, C> {
+  __device__ __forceinline__ static void load(const void* base, int64_t texel, float* v) {
+    const float* p = reinterpret_cast<const float*>(base) + texel * C;
+    if constexpr (C == 4) {
+      const float4 q = __ldg(reinterpret_cast<const float4*>(p));
+      v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+    } else if constexpr (C == 2) {
+      const float2 q = __ldg(reinterpret_cast<const float2*>(p));
+      v[0] = q.x; v[1] = q.y;
+    } else {
+#pragma unroll
+      for (int c = 0; c < C; ++c) v[c] = __ldg(p + c);
+    }
+  }
+};
+
+template <int C> struct TexelIO<STF_FMT_F16, C> {
+  __device__ __forceinline__ static void load(const void* base, int64_t texel, float* v) {
+    const __half* p = reinterpret_cast<const __half*>(base) + texel * C;
+    if constexpr (C == 8) {
+      const uint4 q = __ldg(reinterpret_cast<const uint4*>(p));
+      const __half2* h = reinterpret_cast<const __half2*>(&q);
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const float2 f2 = __half22float2(h[j]);
+        v[2 * j] = f2.x; v[2 * j + 1] = f2.y;
+      }
+    } else if constexpr (C == 4) {
+      const uint2 q = __ldg(reinterpret_cast<const uint2*>(p));
+      const __half2* h = reinterpret_cast<const __half2*>(&q);
+      const float2 a = __half22float2(h[0]), b = __half22float2(h[1]);
+      v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+    } else {
+#pragma unroll
+      for (int c = 0; c < C; ++c) v[c] = __half2float(__ldg(p + c));
+    }
+  }
+};
+
+template <int C>
+__device__ __forceinline__ void store_out(float* out, int64_t i, const float* v) {
+  float* p = out + i * C;
+  if constexpr (C == 4) {
+    *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+  } else if constexpr (C == 8) {
+    reinterpret_cast<float4*>(p)[0] = make_float4(v[0], v[1], v[2], v[3]);
+    reinterpret_cast<float4*>(p)[1] = make_float4(v[4], v[5], v[6], v[7]);
+  } else if constexpr (C == 2) {
+    *reinterpret_cast<float2*>(p) = make_float2(v[0], v[1]);
+  } else {
+#pragma unroll
+    for (int c = 0; c < C; ++c) p[c] = v[c];
+  }
+}
+
+__device__ __forceinline__ bool finite3(float a, float b, float c) {
+  return isfinite(a) && isfinite(b) && isfinite(c);
+}
+
+}  // namespace stf

@@ -1,0 +1,21 @@
+// Internal declarations shared by the host-side translation units.
+#pragma once
+#include <cuda_runtime.h>
+
+#include "stf_launch.h"
+
+namespace stf {
+
+stf_status fail(stf_status code, const char* fmt, ...);
+stf_status fail_cuda(cudaError_t e, const char* what);
+cudaError_t dev_alloc(void** p, size_t bytes);
+bool handle_ok(stf_texture t);
+stf_status dispatch(Op op, stf_texture t, int filter, const LookupArgs& a, cudaStream_t s);
+
+// Sparse grid construction (stf_sparse.cu).
+stf_status build_sparse(stf_texture_s* t, const stf_texture_desc* d, cudaStream_t s);
+
+// Morton-binned stochastic lookup (stf_binning.cu).
+stf_status lookup_binned(stf_texture t, int filter, const LookupArgs& a, cudaStream_t s);
+
+}  // namespace stf

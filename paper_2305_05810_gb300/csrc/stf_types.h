@@ -1,0 +1,57 @@
+// Internal types shared by the library's translation units (not part of the ABI).
+#pragma once
+#include <stdint.h>
+
+#include "../../include/stf.h"
+
+#define STF_MAX_LEVELS 16
+#define STF_TEX_MAGIC 0x53544654u  // "STFT"
+
+// Device status word bits (set by kernels with atomicOr, read by stf_synchronize).
+#define STF_DEV_BAD_NODE 1u        // sparse traversal met an index outside its arrays
+
+namespace stf {
+
+struct SparseDev {
+  // Root: a short list of upper nodes (each covers 4096^3 voxels).
+  int32_t n_upper;
+  const int32_t* upper_origin;     // n_upper x 3
+  const uint64_t* upper_mask;      // n_upper x 512 words (32^3 child bits)
+  const uint32_t* upper_prefix;    // n_upper x 512: set bits before each word
+  const int32_t* upper_lower_base; // n_upper: index of the node's first lower node
+  // Lower nodes (each covers 128^3 voxels, 16^3 leaves).
+  int32_t n_lower;
+  const uint64_t* lower_mask;      // n_lower x 64 words
+  const uint32_t* lower_prefix;    // n_lower x 64
+  const int32_t* lower_leaf_base;  // n_lower
+  // Leaves: 512 values each, [x&7][y&7][z&7].
+  int64_t n_leaves;
+  const float* leaf_f32;           // FP32 format
+  const uint8_t* leaf_e4m3;        // E4M3 format
+  const float* leaf_scale;         // E4M3 format: one scale per leaf
+  float background;
+  unsigned* status;
+};
+
+}  // namespace stf
+
+struct stf_texture_s {
+  uint32_t magic;
+  int32_t kind, format, channels, levels;
+  int32_t dims[3];
+  float background;
+  // 2D / dense texels in storage format
+  void* d_texels;
+  int64_t level_off[STF_MAX_LEVELS];
+  int32_t level_w[STF_MAX_LEVELS];
+  int32_t level_h[STF_MAX_LEVELS];
+  // sparse tree (one allocation, views into it)
+  void* d_tree;
+  stf::SparseDev sparse;
+  // device status word
+  unsigned* d_status;
+  // binning scratch, grown on demand
+  void* d_scratch;
+  int64_t scratch_bytes;
+  int64_t bytes;
+};

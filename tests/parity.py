@@ -1,0 +1,73 @@
+"""Helpers shared by the GPU parity tests: build matching texture stores for the
+library and the oracle, and compare results under the stated tolerances.
+
+Tolerances (from the float32 arithmetic of the kernels):
+* tap indices: bit-exact, except where a variate lies within 1e-6 of a CDF boundary
+  (the oracle reports those as exempt); an exempt tap may differ by one per axis;
+* stochastic values: |gpu - ref| <= 2e-6 |ref| (the texel is exact; only the
+  float32 scale sign(w) * sum|w| of Catmull-Rom carries rounding);
+* deterministic values: |gpu - ref| <= 2e-6 max(|ref|, sum_i |w_i t_i|), the second
+  term covering cancellation between the negative lobes of Catmull-Rom.
+"""
+import itertools
+
+import numpy as np
+import torch
+
+import paper_2305_05810_gb300 as stf
+from oracle import codecs, filters, kernels, textures
+
+REL = 2e-6
+
+
+def dev():
+    return torch.device("cuda:0")
+
+
+def quantise(values, fmt):
+    """Values as the library stores them (exact float64)."""
+    v = np.asarray(values, dtype=np.float32)
+    if fmt == stf.FMT_F16:
+        return codecs.f16_decode(codecs.f16_encode(v.astype(np.float64)))
+    return v.astype(np.float64)
+
+
+def abs_weighted_sum(fetch, xs32, filt):
+    """sum over taps of |w| |t| (tolerance scale for deterministic filters)."""
+    offs, _, _ = kernels.FILTERS[filt]
+    frames = [filters.axis_frame(x) for x in xs32]
+    weights = [np.abs(filters.axis_weights(f, filt)) for (_, f, _) in frames]
+    total = 0.0
+    for combo in itertools.product(range(len(offs)), repeat=len(xs32)):
+        w = np.prod([weights[a][combo[a]] for a in range(len(xs32))], axis=0)
+        total = total + w[:, None] * np.abs(fetch(*[frames[a][0] + offs[combo[a]] for a in range(len(xs32))]))
+    return total
+
+
+def check_stochastic(gpu_val, gpu_taps, ref_val, ref_taps, exempt, dims=3):
+    """Assert tap and value parity; returns the number of exempt queries."""
+    gpu_val = np.asarray(gpu_val, dtype=np.float64).reshape(ref_val.shape)
+    gpu_taps = np.asarray(gpu_taps, dtype=np.int64).reshape(-1, 4)
+    same = np.all(gpu_taps == ref_taps, axis=1)
+    bad = ~same & ~exempt
+    assert not np.any(bad), "tap mismatch at %s: gpu %s ref %s" % (
+        np.nonzero(bad)[0][:5], gpu_taps[bad][:5], ref_taps[bad][:5])
+    near = np.all(np.abs(gpu_taps - ref_taps) <= 1, axis=1)
+    assert np.all(near[exempt]), "exempt tap more than one texel away"
+    err = np.abs(gpu_val - ref_val)[same]
+    lim = REL * np.abs(ref_val)[same] + 1e-30
+    assert np.all(err <= lim), "value mismatch: max rel %g" % np.max(err / np.maximum(np.abs(ref_val[same]), 1e-30))
+    return int(np.sum(~same))
+
+
+def check_deterministic(gpu_val, ref_val, scale):
+    gpu_val = np.asarray(gpu_val, dtype=np.float64).reshape(ref_val.shape)
+    err = np.abs(gpu_val - ref_val)
+    lim = REL * np.maximum(np.abs(ref_val), scale) + 1e-30
+    worst = np.max(err / np.maximum(np.maximum(np.abs(ref_val), scale), 1e-30))
+    assert np.all(err <= lim), "deterministic mismatch: worst rel %g" % worst
+    return worst
+
+
+def to_dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(dev())

@@ -191,6 +191,21 @@ def test_expectation_by_enumeration_equals_deterministic_3d(filt):
     assert np.max(np.abs(e - d)) < 1e-12
 
 
+def test_second_moment_of_two_point_estimator():
+    """Stochastic lerp (Eq. 7) is a two-point distribution: variance f(1-f)(t1-t0)^2."""
+    vals = rng.uniform(-1, 1, (1, 12, 1))
+    tex = textures.Texture2D([vals])
+    x = rng.uniform(0, 10, 300).astype(np.float32)
+    y = np.zeros(300, dtype=np.float32)
+    fetch = lambda ix, iy: tex.fetch(0, ix, iy)
+    m1 = filters.expectation_by_enumeration(fetch, [x, y], "linear")[:, 0]
+    m2 = filters.expectation_by_enumeration(fetch, [x, y], "linear", power=2)[:, 0]
+    i0 = np.floor(x.astype(np.float64)).astype(int)
+    f = x.astype(np.float64) - i0
+    t0, t1 = vals[0, i0, 0], vals[0, np.minimum(i0 + 1, 11), 0]
+    assert np.max(np.abs((m2 - m1 ** 2) - f * (1 - f) * (t1 - t0) ** 2)) < 1e-12
+
+
 def test_tap_counts_are_2n_and_4n():
     calls = []
     g = textures.Dense3D(np.ones((6, 6, 6)))
