@@ -23,7 +23,6 @@ import hashlib
 import json
 import os
 import statistics
-import subprocess
 import sys
 import threading
 import time
@@ -82,62 +81,80 @@ def make_texture(stf, w, fmt=None):
 # ------------------------------------------------------------------ clocks
 
 class ClockSampler:
-    """nvidia-smi samples during the timed region."""
-    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
-              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
-              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    """SM clock and clock-event reasons sampled through NVML (read-only queries)
+    every ~1 ms on a background thread; each sample is time-stamped so that the
+    samples inside the timed window can be picked out."""
+    REASONS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown",
+               0x40: "hw_thermal_slowdown", 0x80: "hw_power_brake_slowdown"}
 
-    def __init__(self, index):
-        self.index = index
-        self.lines = []
-        self.proc = None
+    def __init__(self, torch_index):
+        self.torch_index = torch_index
+        self.samples = []
+        self.max_mhz = None
+        self._stop = threading.Event()
+        self.nv = None
+        self.window = None
 
     def __enter__(self):
+        import ctypes
+        import torch
         try:
-            self.proc = subprocess.Popen(
-                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
-                 "--format=csv,noheader,nounits", "-lms", "100"],
-                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
-            self.t = threading.Thread(target=self._read, daemon=True)
+            nv = ctypes.CDLL("libnvidia-ml.so.1")
+            if nv.nvmlInit_v2() != 0:
+                return self
+            h = ctypes.c_void_p()
+            pr = torch.cuda.get_device_properties(self.torch_index)
+            bus = "%08x:%02x:%02x.0" % (getattr(pr, "pci_domain_id", 0), getattr(pr, "pci_bus_id", 0),
+                                         getattr(pr, "pci_device_id", 0))
+            if nv.nvmlDeviceGetHandleByPciBusId_v2(bus.encode(), ctypes.byref(h)) != 0:
+                if nv.nvmlDeviceGetHandleByIndex_v2(0, ctypes.byref(h)) != 0:
+                    return self
+            mx = ctypes.c_uint()
+            if nv.nvmlDeviceGetMaxClockInfo(h, 1, ctypes.byref(mx)) == 0:
+                self.max_mhz = float(mx.value)
+            reasons_fn = getattr(nv, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+                nv.nvmlDeviceGetCurrentClocksThrottleReasons
+            self.nv, self.h, self.reasons_fn = nv, h, reasons_fn
+            self.t = threading.Thread(target=self._run, daemon=True)
             self.t.start()
-        except (OSError, ValueError):
-            self.proc = None
+        except (OSError, AttributeError):
+            self.nv = None
         return self
 
-    def _read(self):
-        for line in self.proc.stdout:
-            self.lines.append(line.strip())
+    def _run(self):
+        import ctypes
+        clk, rs = ctypes.c_uint(), ctypes.c_ulonglong()
+        while not self._stop.is_set():
+            ok = self.nv.nvmlDeviceGetClockInfo(self.h, 1, ctypes.byref(clk)) == 0
+            ok2 = self.reasons_fn(self.h, ctypes.byref(rs)) == 0
+            if ok:
+                self.samples.append((time.perf_counter(), float(clk.value), rs.value if ok2 else 0))
+            time.sleep(0.001)
+
+    def mark(self, t0, t1):
+        self.window = (t0, t1)
 
     def __exit__(self, *a):
-        if self.proc:
-            self.proc.terminate()
-            try:
-                self.proc.wait(timeout=5)
-            except subprocess.TimeoutExpired:
-                self.proc.kill()
+        self._stop.set()
+        if self.nv is not None:
+            self.t.join(timeout=2)
 
     def summary(self):
-        sm, mx, reasons = [], None, set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
-            f = [x.strip() for x in ln.split(",")]
-            if len(f) < 9:
-                continue
-            try:
-                sm.append(float(f[1]))
-                mx = float(f[2])
-            except ValueError:
-                continue
-            for nm, v in zip(names, f[5:9]):
-                if v.lower() == "active":
-                    reasons.add(nm)
-        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
-                "reasons": sorted(reasons), "samples": len(sm)}
+        sel = self.samples
+        where = "whole run"
+        if self.window:
+            inside = [x for x in self.samples if self.window[0] <= x[0] <= self.window[1]]
+            if inside:
+                sel, where = inside, "timed region"
+        reasons = sorted({nm for (_, _, r) in sel for bit, nm in self.REASONS.items() if r & bit})
+        return {"sm_mhz": statistics.median([c for (_, c, _) in sel]) if sel else None,
+                "sm_max_mhz": self.max_mhz, "reasons": reasons, "samples": len(sel),
+                "window": where, "source": "nvml"}
 
 
 # ------------------------------------------------------------------ timing
 
-def time_steps(torch, fn, steps, warmup, stream, dist=None):
+def time_steps(torch, fn, steps, warmup, stream, dist=None, return_window=False):
     """Per-step CUDA-event durations (ms) of fn() on `stream`, and the total (ms)."""
     for _ in range(warmup):
         fn()
@@ -146,15 +163,19 @@ def time_steps(torch, fn, steps, warmup, stream, dist=None):
         dist.barrier()
     torch.cuda.synchronize()
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
+    t0 = time.perf_counter()
     ev[0].record(stream)
     for k in range(steps):
         fn()
         ev[k + 1].record(stream)
     torch.cuda.synchronize()
+    t1 = time.perf_counter()
     per = [ev[k].elapsed_time(ev[k + 1]) for k in range(steps)]
     total = ev[0].elapsed_time(ev[steps])
     if dist is not None:
         dist.barrier()
+    if return_window:
+        return per, total, (t0, t1)
     return per, total
 
 
@@ -281,14 +302,10 @@ def run_ours(args):
         p = stf.make_params(f)
         return lambda: stf.stf_lookup_batch_deterministic(tex.handle, p, coords, None, n, out, stream)
 
-    gpu_index = torch.cuda.current_device()
-    if os.environ.get("CUDA_VISIBLE_DEVICES"):
-        try:
-            gpu_index = int(os.environ["CUDA_VISIBLE_DEVICES"].split(",")[gpu_index])
-        except ValueError:
-            pass
-    with ClockSampler(gpu_index) as clk:
-        per, total = time_steps(torch, stochastic(), args.steps, args.warmup, stream, dist)
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        per, total, win = time_steps(torch, stochastic(), args.steps, args.warmup, stream, dist,
+                                     return_window=True)
+        clk.mark(*win)
     stf.stf_synchronize(tex.handle, stream)
 
     # max over ranks

@@ -74,13 +74,17 @@ class Dense3D:
 
 class Sparse3D:
     """Leaves: origins (L, 3) int (multiples of 8) and values (L, 8, 8, 8) indexed
-    [x & 7, y & 7, z & 7].  Lookup goes through a sorted key map."""
+    [x & 7, y & 7, z & 7] (float32 or float64, read exactly).  Lookup goes through a
+    sorted key map."""
 
     OFF = 1 << 20
 
     def __init__(self, origins, leaf_values, background=0.0):
-        origins = np.asarray(origins, dtype=np.int64)
-        self.values = np.asarray(leaf_values, dtype=np.float64).reshape(-1, 8, 8, 8)
+        origins = np.asarray(origins, dtype=np.int64).reshape(-1, 3)
+        lv = np.asarray(leaf_values)
+        if lv.dtype not in (np.float32, np.float64):
+            lv = lv.astype(np.float64)
+        self.values = lv.reshape(-1, 8, 8, 8)       # float32 leaves are kept as is (exact)
         keys = self._key(origins[:, 0] >> 3, origins[:, 1] >> 3, origins[:, 2] >> 3)
         order = np.argsort(keys, kind="stable")
         self.keys = keys[order]
@@ -105,5 +109,5 @@ class Sparse3D:
         out = np.full(ix.shape[0], self.background)
         if np.any(hit):
             leaf = self.slot[pos_c[hit]]
-            out[hit] = self.values[leaf, ix[hit] & 7, iy[hit] & 7, iz[hit] & 7]
+            out[hit] = self.values[leaf, ix[hit] & 7, iy[hit] & 7, iz[hit] & 7].astype(np.float64)
         return out[:, None]

@@ -1,6 +1,216 @@
+// Morton-tile binning of queries before a stochastic lookup.
+//
+// Queries are counting-sorted by the Morton code of the spatial tile that holds
+// them, so that the threads of a warp (and the warps of a CTA) gather from nearby
+// texels and the texel traffic hits L2.  The variates stay keyed on the caller's
+// query index and results are written back to the caller's slots, so a binned call
+// returns exactly what the unbinned call returns.
+//
+// Tiles: 16x16 texels of level 0 for 2D (<= 256 x 256 tiles, coordinates wrap);
+// for 3D, cubes of 2^shift voxels with 32 tiles per axis (wrapping beyond), where
+// shift = max(3, ceil(log2(extent / 32))) for dense grids and 6 for sparse grids.
+//
+// Scratch (histogram, cursors, permutation, binned coordinates) comes from a
+// library-owned stream-ordered pool and is released on the same stream after the
+// lookup, so concurrent binned calls on different streams do not share memory.
+#include <mutex>
+
 #include "stf_internal.h"
+
 namespace stf {
-stf_status lookup_binned(stf_texture, int, const LookupArgs&, cudaStream_t) {
-  return fail(STF_ERR_UNSUPPORTED, "binning not built yet");
+
+static constexpr int kBins3D = 32768;
+static constexpr int kBins2D = 65536;
+
+__device__ __forceinline__ uint32_t spread3_5(uint32_t v) {  // 5 bits -> every third bit
+  v &= 31u;
+  v = (v | (v << 8)) & 0x0000F00Fu;
+  v = (v | (v << 4)) & 0x000C30C3u;
+  v = (v | (v << 2)) & 0x00249249u;
+  return v;
 }
+
+__device__ __forceinline__ uint32_t spread2_8(uint32_t v) {  // 8 bits -> every second bit
+  v &= 255u;
+  v = (v | (v << 4)) & 0x0F0Fu;
+  v = (v | (v << 2)) & 0x3333u;
+  v = (v | (v << 1)) & 0x5555u;
+  return v;
 }
+
+struct BinSpec {
+  int dims;        // 2 or 3
+  int shift;       // 3D tile edge = 2^shift voxels
+  float scale_x;   // 2D: level-0 width and height
+  float scale_y;
+};
+
+__device__ __forceinline__ uint32_t bin_key(const BinSpec& b, const float* coords, int64_t i) {
+  if (b.dims == 2) {
+    const float2 uv = reinterpret_cast<const float2*>(coords)[i];
+    const float x = fminf(fmaxf(uv.x * b.scale_x, -1.0e9f), 1.0e9f);
+    const float y = fminf(fmaxf(uv.y * b.scale_y, -1.0e9f), 1.0e9f);
+    const int tx = (int)floorf(x) >> 4, ty = (int)floorf(y) >> 4;   // NaN converts to 0
+    return spread2_8((uint32_t)tx) | (spread2_8((uint32_t)ty) << 1);
+  }
+  const float* p = coords + 3 * i;
+  const int x = (int)floorf(fminf(fmaxf(__ldg(p), -1.0e9f), 1.0e9f));
+  const int y = (int)floorf(fminf(fmaxf(__ldg(p + 1), -1.0e9f), 1.0e9f));
+  const int z = (int)floorf(fminf(fmaxf(__ldg(p + 2), -1.0e9f), 1.0e9f));
+  return spread3_5((uint32_t)(x >> b.shift)) | (spread3_5((uint32_t)(y >> b.shift)) << 1) |
+         (spread3_5((uint32_t)(z >> b.shift)) << 2);
+}
+
+// Histogram with warp-aggregated atomics (lanes sharing a key add once).
+__global__ void __launch_bounds__(256) k_bin_hist(BinSpec b, const float* coords, int64_t n,
+                                                  uint32_t* hist) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n; base += stride) {
+    const int64_t i = base + threadIdx.x;
+    const bool live = i < n;
+    const uint32_t key = live ? bin_key(b, coords, i) : 0xFFFFFFFFu;
+    const unsigned peers = __match_any_sync(0xFFFFFFFFu, key);
+    const int leader = __ffs(peers) - 1;
+    if (live && (threadIdx.x & 31) == leader) atomicAdd(hist + key, (uint32_t)__popc(peers));
+  }
+}
+
+// Exclusive scan of nbins counts into cursors, one 1024-thread block.
+__global__ void __launch_bounds__(1024) k_bin_scan(const uint32_t* hist, uint32_t* cursor,
+                                                   int nbins) {
+  __shared__ uint32_t part[1024];
+  const int per = (nbins + 1023) / 1024;
+  const int lo = threadIdx.x * per, hi = min(lo + per, nbins);
+  uint32_t s = 0;
+  for (int k = lo; k < hi; ++k) s += hist[k];
+  part[threadIdx.x] = s;
+  __syncthreads();
+  for (int off = 1; off < 1024; off <<= 1) {   // Hillis-Steele inclusive scan
+    const uint32_t v = threadIdx.x >= off ? part[threadIdx.x - off] : 0u;
+    __syncthreads();
+    part[threadIdx.x] += v;
+    __syncthreads();
+  }
+  uint32_t run = threadIdx.x ? part[threadIdx.x - 1] : 0u;
+  for (int k = lo; k < hi; ++k) {
+    cursor[k] = run;
+    run += hist[k];
+  }
+}
+
+// Scatter each query to its bin: perm[pos] = i, binned coordinates (and lod).
+__global__ void __launch_bounds__(256) k_bin_scatter(BinSpec b, const float* coords,
+                                                     const float* lod, int64_t n,
+                                                     uint32_t* cursor, uint32_t* perm,
+                                                     float* coords_out, float* lod_out) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int lane = threadIdx.x & 31;
+  for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n; base += stride) {
+    const int64_t i = base + threadIdx.x;
+    const bool live = i < n;
+    const uint32_t key = live ? bin_key(b, coords, i) : 0xFFFFFFFFu;
+    const unsigned peers = __match_any_sync(0xFFFFFFFFu, key);
+    const int leader = __ffs(peers) - 1;
+    uint32_t start = 0;
+    if (live && lane == leader) start = atomicAdd(cursor + key, (uint32_t)__popc(peers));
+    start = __shfl_sync(0xFFFFFFFFu, start, leader);
+    if (!live) continue;
+    const uint32_t pos = start + __popc(peers & ((1u << lane) - 1u));
+    perm[pos] = (uint32_t)i;
+    if (b.dims == 2) {
+      reinterpret_cast<float2*>(coords_out)[pos] = reinterpret_cast<const float2*>(coords)[i];
+      if (lod) lod_out[pos] = lod[i];
+    } else {
+      coords_out[3 * (int64_t)pos] = coords[3 * i];
+      coords_out[3 * (int64_t)pos + 1] = coords[3 * i + 1];
+      coords_out[3 * (int64_t)pos + 2] = coords[3 * i + 2];
+    }
+  }
+}
+
+static std::mutex g_pool_mutex;
+static cudaMemPool_t g_pool[64];
+
+static cudaError_t pool_alloc(void** p, size_t bytes, cudaStream_t s) {
+  *p = nullptr;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  {
+    std::lock_guard<std::mutex> lk(g_pool_mutex);
+    if (!g_pool[dev & 63]) {
+      cudaMemPoolProps props = {};
+      props.allocType = cudaMemAllocationTypePinned;
+      props.location.type = cudaMemLocationTypeDevice;
+      props.location.id = dev;
+      e = cudaMemPoolCreate(&g_pool[dev & 63], &props);
+      if (e != cudaSuccess) return e;
+      uint64_t keep = UINT64_MAX;   // keep freed blocks for reuse by later calls
+      cudaMemPoolSetAttribute(g_pool[dev & 63], cudaMemPoolAttrReleaseThreshold, &keep);
+    }
+  }
+  void* probe = nullptr;
+  e = dev_alloc(&probe, 0);          // honours the failure-injection hook
+  if (e != cudaSuccess) return e;
+  cudaFree(probe);
+  return cudaMallocFromPoolAsync(p, bytes, g_pool[dev & 63], s);
+}
+
+BinSpec bin_spec(const stf_texture_s* t) {
+  BinSpec b;
+  b.dims = t->kind == STF_KIND_TEX2D ? 2 : 3;
+  b.scale_x = (float)t->dims[0];
+  b.scale_y = (float)t->dims[1];
+  if (t->kind == STF_KIND_SPARSE3D) {
+    b.shift = 6;
+  } else {
+    int ext = t->dims[0] > t->dims[1] ? t->dims[0] : t->dims[1];
+    if (t->dims[2] > ext) ext = t->dims[2];
+    int sh = 3;
+    while ((ext >> sh) > 32) ++sh;
+    b.shift = sh;
+  }
+  return b;
+}
+
+stf_status lookup_binned(stf_texture t, int filter, const LookupArgs& a0, cudaStream_t s) {
+  const BinSpec b = bin_spec(t);
+  const int nbins = b.dims == 2 ? kBins2D : kBins3D;
+  const int64_t n = a0.n;
+  if (n > (int64_t)UINT32_MAX) return fail(STF_ERR_INVALID_ARGUMENT, "binned calls take < 2^32 queries");
+  const size_t b_hist = sizeof(uint32_t) * 2 * nbins;
+  const size_t b_perm = (sizeof(uint32_t) * n + 255) & ~(size_t)255;
+  const size_t b_coords = (sizeof(float) * b.dims * n + 255) & ~(size_t)255;
+  const size_t b_lod = a0.lod ? sizeof(float) * n : 0;
+  void* scratch = nullptr;
+  cudaError_t e = pool_alloc(&scratch, b_hist + b_perm + b_coords + b_lod, s);
+  if (e != cudaSuccess) return fail_cuda(e, "binning scratch");
+  char* p = (char*)scratch;
+  uint32_t* hist = (uint32_t*)p;
+  uint32_t* cursor = hist + nbins;
+  uint32_t* perm = (uint32_t*)(p + b_hist);
+  float* coords = (float*)(p + b_hist + b_perm);
+  float* lod = a0.lod ? (float*)(p + b_hist + b_perm + b_coords) : nullptr;
+  e = cudaMemsetAsync(hist, 0, sizeof(uint32_t) * nbins, s);
+  const int blocks = grid_blocks(n, 256);
+  if (e == cudaSuccess) {
+    k_bin_hist<<<blocks, 256, 0, s>>>(b, a0.coords, n, hist);
+    k_bin_scan<<<1, 1024, 0, s>>>(hist, cursor, nbins);
+    k_bin_scatter<<<blocks, 256, 0, s>>>(b, a0.coords, a0.lod, n, cursor, perm, coords, lod);
+    e = cudaGetLastError();
+  }
+  stf_status st = STF_OK;
+  if (e != cudaSuccess) {
+    st = fail_cuda(e, "binning launch");
+  } else {
+    LookupArgs a = a0;
+    a.coords = coords;
+    a.lod = lod;
+    a.perm = perm;
+    st = dispatch(OP_STOCHASTIC, t, filter, a, s);
+  }
+  cudaFreeAsync(scratch, s);
+  return st;
+}
+
+}  // namespace stf

@@ -60,16 +60,18 @@ template <> struct Filter<STF_FILTER_BSPLINE3> {
   }
 };
 
-// Cubic K3 with a = -1/2 (Appendix A), Catmull-Rom: -f g^2 / 2, 1 + f^2(3f/2 - 5/2),
-// 1 + g^2(3g/2 - 5/2), -g f^2 / 2.
+// Cubic K3 with a = -1/2 (Appendix A), Catmull-Rom.  The inner piece
+// 1 - 5/2 t^2 + 3/2 t^3 is factored as (1 - t)(1 + t(1 - 3t/2)) so that the taps at
+// t = f and t = 1 - f carry no cancellation near f = 0 or 1 (1 - t is then the exact
+// g or f):  -f g^2/2,  g(1 + f(1 - 3f/2)),  f(1 + g(1 - 3g/2)),  -g f^2/2.
 template <> struct Filter<STF_FILTER_CATMULL_ROM> {
   static constexpr int T = 4, OFF0 = -1;
   static constexpr bool NONNEG = false;
   __device__ __forceinline__ static void weights(float f, float* w) {
     const float g = 1.0f - f;
     w[0] = -0.5f * f * g * g;
-    w[1] = fmaf(f * f, fmaf(1.5f, f, -2.5f), 1.0f);
-    w[2] = fmaf(g * g, fmaf(1.5f, g, -2.5f), 1.0f);
+    w[1] = g * fmaf(f, fmaf(-1.5f, f, 1.0f), 1.0f);
+    w[2] = f * fmaf(g, fmaf(-1.5f, g, 1.0f), 1.0f);
     w[3] = -0.5f * g * f * f;
   }
 };
@@ -148,7 +150,14 @@ struct LookupArgs {
   int32_t n_samples;      // accumulate kernels
   double* sum;
   double* sumsq;
+  // Binned calls: coords/lod are in binned order and perm[i] is the caller's index
+  // of binned query i (it keys the generator and picks the output slot).
+  const uint32_t* perm;
 };
+
+__device__ __forceinline__ int64_t query_slot(const LookupArgs& a, int64_t i) {
+  return a.perm ? (int64_t)__ldg(a.perm + i) : i;
+}
 
 template <int FMT, int C> struct TexelIO;
 

@@ -23,8 +23,8 @@ __device__ __forceinline__ int level_stochastic(const Tex2DView& t, const Lookup
 
 template <int F, int FMT, int C>
 __device__ __forceinline__ void tex2d_stochastic_one(const Tex2DView& t, const LookupArgs& a,
-                                                     int64_t i, uint32_t sample, float* v,
-                                                     int4& tap) {
+                                                     int64_t i, int64_t j, uint32_t sample,
+                                                     float* v, int4& tap) {
   using Fl = Filter<F>;
   const float2 uv = reinterpret_cast<const float2*>(a.coords)[i];
   const float lod = a.lod ? a.lod[i] : 0.0f;
@@ -34,7 +34,7 @@ __device__ __forceinline__ void tex2d_stochastic_one(const Tex2DView& t, const L
     tap = make_int4(0, 0, 0, -1);
     return;
   }
-  const uint64_t q = a.query_offset + (uint64_t)i;
+  const uint64_t q = a.query_offset + (uint64_t)j;
   const uint4 r = philox4x32_10(make_uint4((uint32_t)q, (uint32_t)(q >> 32), sample, 0u),
                                 a.key0, a.key1);
   const int L = level_stochastic(t, a, lod, unit24(r.w));
@@ -97,9 +97,10 @@ __global__ void __launch_bounds__(256) k_tex2d_stochastic(Tex2DView t, LookupArg
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += stride) {
     float v[C];
     int4 tap;
-    tex2d_stochastic_one<F, FMT, C>(t, a, i, a.sample_index, v, tap);
-    store_out<C>(a.out, i, v);
-    if (a.taps) reinterpret_cast<int4*>(a.taps)[i] = tap;
+    const int64_t j = query_slot(a, i);
+    tex2d_stochastic_one<F, FMT, C>(t, a, i, j, a.sample_index, v, tap);
+    store_out<C>(a.out, j, v);
+    if (a.taps) reinterpret_cast<int4*>(a.taps)[j] = tap;
   }
 }
 
@@ -143,7 +144,7 @@ __global__ void __launch_bounds__(256) k_tex2d_accumulate(Tex2DView t, LookupArg
     for (int k = 0; k < a.n_samples; ++k) {
       float v[C];
       int4 tap;
-      tex2d_stochastic_one<F, FMT, C>(t, a, i, a.sample_index + (uint32_t)k, v, tap);
+      tex2d_stochastic_one<F, FMT, C>(t, a, i, i, a.sample_index + (uint32_t)k, v, tap);
 #pragma unroll
       for (int c = 0; c < C; ++c) {
         s[c] += (double)v[c];
@@ -174,7 +175,8 @@ __device__ __forceinline__ float dense_fetch(const Dense3DView& g, int ix, int i
 
 template <int F, int FMT>
 __device__ __forceinline__ float dense_stochastic_one(const Dense3DView& g, const LookupArgs& a,
-                                                      int64_t i, uint32_t sample, int4& tap) {
+                                                      int64_t i, int64_t j, uint32_t sample,
+                                                      int4& tap) {
   using Fl = Filter<F>;
   const float px = __ldg(a.coords + 3 * i), py = __ldg(a.coords + 3 * i + 1),
               pz = __ldg(a.coords + 3 * i + 2);
@@ -182,7 +184,7 @@ __device__ __forceinline__ float dense_stochastic_one(const Dense3DView& g, cons
     tap = make_int4(0, 0, 0, -1);
     return g.background;
   }
-  const uint64_t q = a.query_offset + (uint64_t)i;
+  const uint64_t q = a.query_offset + (uint64_t)j;
   const uint4 r = philox4x32_10(make_uint4((uint32_t)q, (uint32_t)(q >> 32), sample, 0u),
                                 a.key0, a.key1);
   float fx, fy, fz;
@@ -207,8 +209,9 @@ __global__ void __launch_bounds__(256) k_dense_stochastic(Dense3DView g, LookupA
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += stride) {
     int4 tap;
-    a.out[i] = dense_stochastic_one<F, FMT>(g, a, i, a.sample_index, tap);
-    if (a.taps) reinterpret_cast<int4*>(a.taps)[i] = tap;
+    const int64_t j = query_slot(a, i);
+    a.out[j] = dense_stochastic_one<F, FMT>(g, a, i, j, a.sample_index, tap);
+    if (a.taps) reinterpret_cast<int4*>(a.taps)[j] = tap;
   }
 }
 
@@ -251,7 +254,7 @@ __global__ void __launch_bounds__(256) k_dense_accumulate(Dense3DView g, LookupA
     double s = 0.0, s2 = 0.0;
     for (int k = 0; k < a.n_samples; ++k) {
       int4 tap;
-      const double v = dense_stochastic_one<F, FMT>(g, a, i, a.sample_index + (uint32_t)k, tap);
+      const double v = dense_stochastic_one<F, FMT>(g, a, i, i, a.sample_index + (uint32_t)k, tap);
       s += v;
       s2 += v * v;
     }

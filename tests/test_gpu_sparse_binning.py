@@ -1,0 +1,191 @@
+"""GPU parity: sparse grids (FP32 and scaled E4M3 leaves) and Morton-binned calls."""
+import numpy as np
+import pytest
+import torch
+
+import paper_2305_05810_gb300 as stf
+import synth
+from oracle import codecs, filters, textures
+from parity import (abs_weighted_sum, check_deterministic, check_stochastic, dev, quantise,
+                    to_dev)
+
+pytestmark = pytest.mark.gpu
+FILTERS = ["linear", "bspline3", "catmull_rom"]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    stf.load()
+
+
+def sparse_pair(origins, values, fmt, background=0.0):
+    """(library texture, oracle store) holding the same leaves."""
+    T = stf.Texture(stf.KIND_SPARSE3D, values, fmt=fmt, leaf_origins=origins, background=background)
+    if fmt == stf.FMT_E4M3_SCALED:
+        codes, scales = codecs.e4m3_leaf_quantise(values)
+        stored = codecs.e4m3_leaf_dequantise(codes, scales)
+    else:
+        stored = np.asarray(values, dtype=np.float32)
+    return T, textures.Sparse3D(origins, stored, background)
+
+
+def _points(domain, n, seed):
+    p = synth.uniform(3 * n, seed).reshape(-1, 3) * np.float32(domain + 16) - np.float32(8)
+    edge = np.array([[np.nan, 1, 1], [-3.5, 2, 2], [domain - 0.25, 5, 9], [1e9, 0, 0],
+                     [-5000.0, -5000.0, 7.0]], dtype=np.float32)
+    return np.concatenate([p.astype(np.float32), edge])
+
+
+@pytest.mark.parametrize("fmt", [stf.FMT_F32, stf.FMT_E4M3_SCALED])
+@pytest.mark.parametrize("filt", FILTERS)
+def test_sparse_cloud_matches_oracle(filt, fmt):
+    origins, values = synth.sparse_cloud(domain=256, seed=4)
+    T, ref = sparse_pair(origins, values, fmt)
+    # half the queries near active leaves so that most taps hit stored voxels
+    near = (origins[np.arange(20000) % len(origins)]
+            + synth.uniform(60000, 10).reshape(-1, 3) * np.float32(8)).astype(np.float32)
+    pts = np.concatenate([_points(256, 20000, 5), near])
+    N = pts.shape[0]
+    taps = torch.empty((N, 4), dtype=torch.int32, device=dev())
+    out = T.lookup(to_dev(pts), taps=taps, filter=filt, seed=99)
+    rv, rt, ex = filters.lookup_3d(ref, pts, filt, stochastic_form=True, seed=99)
+    torch.cuda.synchronize()
+    check_stochastic(out.cpu().numpy(), taps.cpu().numpy(), rv, rt, ex)
+    det = T.lookup_deterministic(to_dev(pts), filter=filt)
+    dv, _, _ = filters.lookup_3d(ref, pts, filt, stochastic_form=False)
+    scale = abs_weighted_sum(ref.fetch, [pts[:, 0], pts[:, 1], pts[:, 2]], filt)
+    check_deterministic(det.cpu().numpy(), dv, np.nan_to_num(scale))
+    stf.stf_synchronize(T.handle)
+
+
+def test_sparse_several_upper_nodes_and_negative_coordinates():
+    origins = np.array([[0, 0, 0], [8, 0, 0], [4096, 0, 0], [-4096, 8, 16], [-8, -8, -8],
+                        [8192, 8192, 8192], [4088, 0, 0]], dtype=np.int32)
+    values = synth.uniform(len(origins) * 512, 3).reshape(-1, 512) + np.float32(0.1)
+    T, ref = sparse_pair(origins, values, stf.FMT_F32, background=0.25)
+    pts = (origins[np.arange(30000) % len(origins)] +
+           synth.uniform(90000, 6).reshape(-1, 3) * np.float32(12) - np.float32(2)).astype(np.float32)
+    N = pts.shape[0]
+    for filt in FILTERS:
+        taps = torch.empty((N, 4), dtype=torch.int32, device=dev())
+        out = T.lookup(to_dev(pts), taps=taps, filter=filt, seed=1)
+        rv, rt, ex = filters.lookup_3d(ref, pts, filt, stochastic_form=True, seed=1)
+        torch.cuda.synchronize()
+        check_stochastic(out.cpu().numpy(), taps.cpu().numpy(), rv, rt, ex)
+        det = T.lookup_deterministic(to_dev(pts), filter=filt)
+        dv, _, _ = filters.lookup_3d(ref, pts, filt, stochastic_form=False)
+        check_deterministic(det.cpu().numpy(), dv, 1.0)
+    stf.stf_synchronize(T.handle)
+
+
+def test_sparse_empty_grid_and_invalid_leaves():
+    pts = _points(64, 1000, 2)
+    T = stf.Texture(stf.KIND_SPARSE3D, np.zeros((0, 512), np.float32), leaf_origins=np.zeros((0, 3), np.int32),
+                    background=0.5)
+    out = T.lookup(to_dev(pts), filter="bspline3")
+    det = T.lookup_deterministic(to_dev(pts), filter="catmull_rom")
+    o = out.cpu().numpy()[:, 0]
+    assert np.all(o == 0.5)
+    assert np.allclose(det.cpu().numpy()[:-5, 0], 0.5, rtol=1e-6)
+    vals = np.ones((2, 512), np.float32)
+    with pytest.raises(stf.StfError) as e:
+        stf.Texture(stf.KIND_SPARSE3D, vals, leaf_origins=np.array([[0, 0, 0], [0, 0, 0]], np.int32))
+    assert e.value.status == 1
+    with pytest.raises(stf.StfError) as e:
+        stf.Texture(stf.KIND_SPARSE3D, vals, leaf_origins=np.array([[0, 0, 0], [4, 0, 0]], np.int32))
+    assert e.value.status == 1
+
+
+def test_sparse_e4m3_storage_error_vs_fp32():
+    """Stated FP8 error: deterministic tricubic on E4M3 leaves against the float64
+    filter of the unquantised values (relative to the filtered magnitude)."""
+    origins, values = synth.sparse_cloud(domain=256, seed=4)
+    T, _ = sparse_pair(origins, values, stf.FMT_E4M3_SCALED)
+    exact = textures.Sparse3D(origins, values)
+    pts = (origins[np.arange(50000) % len(origins)] + synth.uniform(150000, 12).reshape(-1, 3)
+           * np.float32(8)).astype(np.float32)
+    det = T.lookup_deterministic(to_dev(pts), filter="bspline3").cpu().numpy()[:, 0]
+    dv, _, _ = filters.lookup_3d(exact, pts, "bspline3", stochastic_form=False)
+    rel = np.abs(det - dv[:, 0]) / np.maximum(np.abs(dv[:, 0]), 1e-3)
+    assert np.median(rel) < 0.02 and np.percentile(rel, 99) < 0.0625, (np.median(rel), np.percentile(rel, 99))
+
+
+# ------------------------------------------------------------------ binning
+
+def _same_binned(T, coords, lod=None, **kw):
+    N = coords.shape[0]
+    t1 = torch.empty((N, 4), dtype=torch.int32, device=dev())
+    t2 = torch.empty((N, 4), dtype=torch.int32, device=dev())
+    a = T.lookup(coords, lod, taps=t1, **kw)
+    b = T.lookup(coords, lod, taps=t2, bin_queries=True, **kw)
+    torch.cuda.synchronize()
+    assert torch.equal(a, b) and torch.equal(t1, t2)
+
+
+@pytest.mark.parametrize("filt", FILTERS)
+def test_binned_equals_unbinned_dense_and_2d(filt):
+    vals = synth.dense_density(n=64, seed=3, period=12.0)
+    T = stf.Texture(stf.KIND_DENSE3D, vals, dims=(64, 64, 64), fmt=stf.FMT_F16)
+    q = synth.camera_queries(W=160, H=90, steps=16, centre=(32, 32, 32), radius=96, half_span=56, seed=3)
+    _same_binned(T, to_dev(q), filter=filt, seed=5, query_offset=17)
+    img = synth.texture2d(128, 64, 4, seed=2)
+    T2 = stf.Texture(stf.KIND_TEX2D, img, dims=(128, 64, 1), channels=4, mip_levels=8, generate_mips=True)
+    uv = to_dev(synth.uv_queries(70001, seed=8))
+    lod = to_dev(synth.lods(70001, seed=9, lo=0, hi=7))
+    _same_binned(T2, uv, lod, filter=filt, seed=6)
+    _same_binned(T2, uv, None, filter=filt, seed=6)
+
+
+def test_binned_equals_unbinned_sparse():
+    origins, values = synth.sparse_cloud(domain=512, seed=4)
+    T = stf.Texture(stf.KIND_SPARSE3D, values, fmt=stf.FMT_E4M3_SCALED, leaf_origins=origins)
+    q = synth.camera_queries(W=320, H=320, steps=16, centre=(256, 256, 256), radius=768,
+                             half_span=444, seed=4)
+    for filt in FILTERS:
+        _same_binned(T, to_dev(q), filter=filt, seed=7)
+
+
+def _touched_leaves(origins, pts):
+    """Indices of the leaves any 4x4x4 tap window around pts can reach."""
+    base = np.floor(pts[np.all(np.isfinite(pts), axis=1)]).astype(np.int64)
+    cells = set()
+    for d in ((-1, -1, -1), (2, 2, 2), (-1, 2, 2), (2, -1, 2), (2, 2, -1), (-1, -1, 2), (-1, 2, -1),
+              (2, -1, -1)):
+        c = (base + np.array(d)) >> 3
+        cells.update(map(tuple, c.tolist()))
+    key = {tuple(o): i for i, o in enumerate((origins >> 3).tolist())}
+    return np.array(sorted(key[c] for c in cells if c in key), dtype=np.int64)
+
+
+def test_full_size_sparse_ray_march_sampled():
+    """2048^3 domain, ~4% active leaves, 2048x2048 rays x 16 steps (67,108,864 queries),
+    FP32 and E4M3 leaves, tricubic; checked on a seeded sample of queries against an
+    oracle store holding every leaf those queries can reach."""
+    origins, values = synth.sparse_cloud(domain=2048, seed=4)
+    assert 0.038 < len(origins) / 256 ** 3 < 0.042
+    q = synth.camera_queries(**synth.C3_RAYS)
+    d = to_dev(q)
+    N = q.shape[0]
+    idx = np.sort(np.random.default_rng(1).choice(N, 1 << 14, replace=False))
+    sub = _touched_leaves(origins, q[idx])
+    for fmt in (stf.FMT_F32, stf.FMT_E4M3_SCALED):
+        T = stf.Texture(stf.KIND_SPARSE3D, values, fmt=fmt, leaf_origins=origins)
+        if fmt == stf.FMT_E4M3_SCALED:
+            codes, scales = codecs.e4m3_leaf_quantise(values[sub])
+            ref = textures.Sparse3D(origins[sub], codecs.e4m3_leaf_dequantise(codes, scales))
+        else:
+            ref = textures.Sparse3D(origins[sub], values[sub])
+        taps = torch.empty((N, 4), dtype=torch.int32, device=dev())
+        sto = T.lookup(d, taps=taps, filter="bspline3", seed=3)
+        rv, rt, ex = filters.lookup_3d(ref, q[idx], "bspline3", stochastic_form=True, seed=3,
+                                       qid=idx.astype(np.uint64))
+        check_stochastic(sto.cpu().numpy()[idx], taps.cpu().numpy()[idx], rv, rt, ex)
+        det = T.lookup_deterministic(d, filter="bspline3")
+        dv, _, _ = filters.lookup_3d(ref, q[idx], "bspline3", stochastic_form=False)
+        check_deterministic(det.cpu().numpy()[idx], dv, 0.0)
+        stf.stf_synchronize(T.handle)
+        T.close()
+        del taps, sto, det
+        torch.cuda.empty_cache()
