@@ -34,6 +34,8 @@ sys.path.insert(0, ROOT)
 
 ALGO_BYTES = {  # algorithmic bytes per lookup: query in + texel(s) + result out
     ("dense", "stochastic"): 12 + 2 + 4,
+    ("sparse", "stochastic"): 12 + 4 + 4,
+    ("sparse_e4m3", "stochastic"): 12 + 1 + 4 + 4,
     ("dense", "deterministic", "bspline3"): 12 + 64 * 2 + 4,
     ("dense", "deterministic", "linear"): 12 + 8 * 2 + 4,
     ("tex2d", "stochastic"): 8 + 16 + 16,
@@ -48,7 +50,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="dense", choices=["dense", "tex2d"])
+    ap.add_argument("--workload", default="dense", choices=["dense", "tex2d", "sparse", "sparse_e4m3"])
     ap.add_argument("--filter", default="bspline3", choices=["linear", "bspline3", "catmull_rom"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--quick", action="store_true", help="skip the extra variants")
@@ -64,6 +66,14 @@ def make_workload(name):
         q = synth.camera_queries(**synth.C2_RAYS)
         desc = "dense 256^3 FP16 fractal-noise density (30% non-zero), 1920x1080 rays x 16 steps"
         return dict(name=name, values=vals, coords=q, dims=(256, 256, 256), channels=1, desc=desc)
+    if name.startswith("sparse"):
+        origins, values = synth.sparse_cloud(domain=2048, seed=4)
+        q = synth.camera_queries(**synth.C3_RAYS)
+        fmt = "E4M3 + per-leaf scale" if name == "sparse_e4m3" else "FP32"
+        desc = ("sparse 2048^3 cloud, %d active 8^3 leaves (%.1f%%), %s, 2048x2048 rays x 16 steps"
+                % (len(origins), 100.0 * len(origins) / 256 ** 3, fmt))
+        return dict(name=name, values=values, origins=origins, coords=q, dims=(0, 0, 0),
+                    channels=1, desc=desc)
     tex = synth.texture2d(256, 256, 4, seed=1)
     n = 1 << 24
     uv = synth.uv_queries(n, seed=2)
@@ -75,6 +85,9 @@ def make_texture(stf, w, fmt=None):
     if w["name"] == "dense":
         return stf.Texture(stf.KIND_DENSE3D, w["values"], dims=w["dims"],
                            fmt=stf.FMT_F16 if fmt is None else fmt)
+    if w["name"].startswith("sparse"):
+        f = stf.FMT_E4M3_SCALED if w["name"] == "sparse_e4m3" else stf.FMT_F32
+        return stf.Texture(stf.KIND_SPARSE3D, w["values"], fmt=f, leaf_origins=w["origins"])
     return stf.Texture(stf.KIND_TEX2D, w["values"], dims=w["dims"], channels=4)
 
 
@@ -218,11 +231,28 @@ def peaks():
 
 # ------------------------------------------------------------------ CPU oracle
 
+def touched_leaves(origins, pts):
+    """Indices of the leaves a 4x4x4 tap window around any of pts can reach."""
+    base = np.floor(pts[np.all(np.abs(pts) < 1e7, axis=1)]).astype(np.int64)
+    key = lambda c: (c[:, 0] + 4096) * (1 << 26) + (c[:, 1] + 4096) * (1 << 13) + (c[:, 2] + 4096)
+    cells = np.unique(np.concatenate([key((base + np.array(d)) >> 3) for d in
+                                      [(a, b, c) for a in (-1, 2) for b in (-1, 2) for c in (-1, 2)]]))
+    ok = key(origins.astype(np.int64) >> 3)
+    return np.nonzero(np.isin(ok, cells))[0]
+
+
 def cpu_oracle_rate(w, filt, n_queries):
     """Oracle lookups/s on the first n_queries queries (stochastic), chunked."""
     from oracle import codecs, filters, textures
     if w["name"] == "dense":
         ref = textures.Dense3D(codecs.f16_decode(codecs.f16_encode(w["values"].astype(np.float64))))
+    elif w["name"].startswith("sparse"):
+        sub = touched_leaves(w["origins"], w["coords"][:n_queries])
+        vals = w["values"][sub]
+        if w["name"] == "sparse_e4m3":
+            codes, scales = codecs.e4m3_leaf_quantise(vals)
+            vals = codecs.e4m3_leaf_dequantise(codes, scales)
+        ref = textures.Sparse3D(w["origins"][sub], vals)
     else:
         ref = textures.Texture2D([w["values"].astype(np.float64)])
     q = w["coords"][:n_queries]
@@ -230,7 +260,7 @@ def cpu_oracle_rate(w, filt, n_queries):
     for a in range(0, q.shape[0], 1 << 20):
         b = min(q.shape[0], a + (1 << 20))
         qid = np.arange(a, b, dtype=np.uint64)
-        if w["name"] == "dense":
+        if w["name"] != "tex2d":
             filters.lookup_3d(ref, q[a:b], filt, stochastic_form=True, seed=1, qid=qid)
         else:
             filters.lookup_2d(ref, q[a:b], None, filt, stochastic_form=True, seed=1, qid=qid)
@@ -245,7 +275,7 @@ def run_reference(args):
     if rank != 0:
         return 0
     w = make_workload(args.workload)
-    n_sample = 1 << 21
+    n_sample = 1 << 20 if args.workload.startswith("sparse") else 1 << 21
     rates = []
     for k in range(args.warmup + args.steps):
         r, _ = cpu_oracle_rate(w, args.filter, n_sample)
@@ -366,7 +396,7 @@ def run_ours(args):
         "value": value, "unit": "lookups/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32 (fp16 texels)" if w["name"] == "dense" else "f32",
+        "dtype": {"dense": "f32 (fp16 texels)", "sparse_e4m3": "f32 (e4m3 texels)"}.get(w["name"], "f32"),
         "data": "synthetic",
         "config": {"workload": w["desc"], "filter": filt, "queries_per_step": n,
                    "l2": "inputs larger than L2 (query+output arrays %d MB per step)"
@@ -384,10 +414,11 @@ def run_ours(args):
         "extras": extras,
     }
     if not args.no_cpu_baseline:
-        rate, dt = cpu_oracle_rate(w, filt, 1 << 23)
+        ns = (1 << 21) if w["name"].startswith("sparse") else (1 << 23)
+        rate, dt = cpu_oracle_rate(w, filt, ns)
         line["cpu_baseline"] = {"value": rate, "unit": "lookups/s", "cores": 1, "kind": "oracle",
                                 "sample": "first %d queries of the workload, stochastic %s, "
-                                          "%.1f s" % (1 << 23, filt, dt)}
+                                          "%.1f s" % (ns, filt, dt)}
     print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()

@@ -141,7 +141,10 @@ stf_status stf_create_texture(const stf_texture_desc* d, void* stream, stf_textu
   if (!out) return fail(STF_ERR_INVALID_ARGUMENT, "out handle pointer is NULL");
   *out = nullptr;
   if (!d) return fail(STF_ERR_INVALID_ARGUMENT, "descriptor is NULL");
-  if (!d->data) return fail(STF_ERR_INVALID_ARGUMENT, "descriptor data is NULL");
+  const bool empty_sparse = d->kind == STF_KIND_SPARSE3D && d->num_leaves == 0;
+  if (!d->data && !empty_sparse) return fail(STF_ERR_INVALID_ARGUMENT, "descriptor data is NULL");
+  if (d->data_on_device && ((uintptr_t)d->data % 16))
+    return fail(STF_ERR_INVALID_ARGUMENT, "device data must be 16-byte aligned");
   cudaStream_t s = (cudaStream_t)stream;
   stf_texture_s* t = new stf_texture_s();
   memset(t, 0, sizeof(*t));

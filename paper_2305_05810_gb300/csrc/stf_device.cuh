@@ -77,48 +77,96 @@ template <> struct Filter<STF_FILTER_CATMULL_ROM> {
 };
 
 // ---------------------------------------------------------------- tap choice
-// Smallest k with u*S < C_k, C_k = running float32 sum of |w_j|, S = C_{T-1}
-// (sampling arrays, Section 2.2); if rounding leaves none, the last tap with
-// |w| > 0.  Returns k; S, sign(w_k) and the Eq. 4 remapped variate through the
-// references.
+// Inverse CDF over |w| (sampling arrays, Section 2.2): tap k is the smallest k with
+// u*S < C_k, C_k = running float32 sum of |w_j|, S = C_{T-1}.  Because u <= 1 - 2^-24
+// and S >= 1, the float32 product u*S is always below S, so that k equals the
+// number of interior boundaries C_0 .. C_{T-2} that are <= u*S; zero-weight taps
+// (C_k == C_{k-1}) are skipped by construction.
 template <int T>
-__device__ __forceinline__ int choose_tap(float u, const float* w, float& S, float& sgn,
-                                          float& u_next) {
-  float c[T];
-  float acc = 0.0f;
-  int last_nz = 0;
+struct TapPick {
+  int k;
+  float S;     // sum |w|
+  float us;    // u * S
+  float c[T];  // running sums
+};
+
+template <int T>
+__device__ __forceinline__ TapPick<T> choose_tap(float u, const float* w) {
+  TapPick<T> p;
+  p.c[0] = fabsf(w[0]);
 #pragma unroll
-  for (int k = 0; k < T; ++k) {
-    const float a = fabsf(w[k]);
-    acc = __fadd_rn(acc, a);
-    c[k] = acc;
-    if (a > 0.0f) last_nz = k;
-  }
-  S = acc;
-  const float us = __fmul_rn(u, S);
-  int k = last_nz;
+  for (int k = 1; k < T; ++k) p.c[k] = __fadd_rn(p.c[k - 1], fabsf(w[k]));
+  p.S = p.c[T - 1];
+  p.us = __fmul_rn(u, p.S);
+  int k = 0;
 #pragma unroll
-  for (int j = T - 1; j >= 0; --j)
-    if (us < c[j]) k = j;
-  float cprev = 0.0f, wk = 0.0f;
-  sgn = 1.0f;
-#pragma unroll
-  for (int j = 0; j < T; ++j) {
-    if (j == k) {
-      wk = fabsf(w[j]);
-      sgn = w[j] < 0.0f ? -1.0f : 1.0f;
-    }
-    if (j + 1 == k) cprev = c[j];
-  }
-  u_next = fminf(fmaxf(__fdiv_rn(__fsub_rn(us, cprev), wk), 0.0f), 0x1.fffffep-1f);
-  return k;
+  for (int j = 0; j < T - 1; ++j) k += (p.us >= p.c[j]) ? 1 : 0;
+  p.k = k;
+  return p;
 }
 
-// Integer tap base floor(x) (clamped to +-2^24) and fraction x - floor(x).
+// Sign of the chosen weight for the Catmull-Rom window, whose taps carry the signs
+// (-, +, +, -); a zero weight is never chosen.
+__device__ __forceinline__ float cr_sign(int k) { return ((k + 1) & 2) ? 1.0f : -1.0f; }
+
+// Eq. 4 generalised to T taps: u' = (u*S - C_{k-1}) / |w_k|, kept in [0, 1).
+template <int T>
+__device__ __forceinline__ float remap_variate(const TapPick<T>& p, const float* w) {
+  float cprev = 0.0f, wk = 1.0f;
+#pragma unroll
+  for (int j = 0; j < T; ++j) {
+    if (j == p.k) wk = fabsf(w[j]);
+    if (j + 1 == p.k) cprev = p.c[j];
+  }
+  return fminf(fmaxf(__fdiv_rn(__fsub_rn(p.us, cprev), wk), 0.0f), 0x1.fffffep-1f);
+}
+
+// Integer tap base floor(x) and fraction x - floor(x); |x| < 2^24 here.
 __device__ __forceinline__ int axis_base(float x, float& f) {
   const float fl = floorf(x);
   f = __fsub_rn(x, fl);
-  return (int)fminf(fmaxf(fl, -16777216.0f), 16777216.0f);
+  return (int)fl;
+}
+
+// Coordinates are used as is when every |x| < 2^24.  Otherwise: a NaN or infinity
+// makes the query return the background value (false); finite values beyond 2^24
+// (all integers in float32) are clamped to +-2^24, which leaves floor(x) = +-2^24
+// and fraction 0, the same as clamping floor(x).
+template <int D>
+__device__ __forceinline__ bool prepare_coords(float* x) {
+  bool small = true;
+#pragma unroll
+  for (int a = 0; a < D; ++a) small = small && fabsf(x[a]) < 16777216.0f;
+  if (small) return true;
+#pragma unroll
+  for (int a = 0; a < D; ++a) {
+    if (!isfinite(x[a])) return false;
+    x[a] = fminf(fmaxf(x[a], -16777216.0f), 16777216.0f);
+  }
+  return true;
+}
+
+// One tap per axis for a D-dimensional separable filter.  u[a] is axis a's own
+// variate; with REUSE only u[0] is used and carried across axes by Eq. 4.
+// Returns the tap coordinates and the estimator's scale sigma (prod sign * S for
+// Catmull-Rom, exactly 1 for the non-negative kernels).
+template <int F, int D, bool REUSE>
+__device__ __forceinline__ float pick_taps(const float* x, const float* u, int* idx) {
+  using Fl = Filter<F>;
+  float sigma = 1.0f;
+  float uc = u[0];
+#pragma unroll
+  for (int a = 0; a < D; ++a) {
+    float f;
+    const int b = axis_base(x[a], f);
+    float w[Fl::T];
+    Fl::weights(f, w);
+    const TapPick<Fl::T> p = choose_tap<Fl::T>(REUSE ? uc : u[a], w);
+    if constexpr (REUSE) uc = remap_variate<Fl::T>(p, w);
+    if constexpr (!Fl::NONNEG) sigma *= cr_sign(p.k) * p.S;
+    idx[a] = b + Fl::OFF0 + p.k;
+  }
+  return sigma;
 }
 
 // ---------------------------------------------------------------- views
@@ -157,6 +205,12 @@ struct LookupArgs {
 
 __device__ __forceinline__ int64_t query_slot(const LookupArgs& a, int64_t i) {
   return a.perm ? (int64_t)__ldg(a.perm + i) : i;
+}
+
+// Philox variates of the caller's query j for one sample index.
+__device__ __forceinline__ uint4 query_variates(const LookupArgs& a, int64_t j, uint32_t sample) {
+  const uint64_t q = a.query_offset + (uint64_t)j;
+  return philox4x32_10(make_uint4((uint32_t)q, (uint32_t)(q >> 32), sample, 0u), a.key0, a.key1);
 }
 
 template <int FMT, int C> struct TexelIO;

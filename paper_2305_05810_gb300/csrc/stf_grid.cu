@@ -21,40 +21,30 @@ __device__ __forceinline__ int level_stochastic(const Tex2DView& t, const Lookup
   return min((int)floorf(s), t.levels - 1);
 }
 
-template <int F, int FMT, int C>
+template <int F, int FMT, int C, bool REUSE>
 __device__ __forceinline__ void tex2d_stochastic_one(const Tex2DView& t, const LookupArgs& a,
                                                      int64_t i, int64_t j, uint32_t sample,
                                                      float* v, int4& tap) {
-  using Fl = Filter<F>;
   const float2 uv = reinterpret_cast<const float2*>(a.coords)[i];
   const float lod = a.lod ? a.lod[i] : 0.0f;
-  if (!finite3(uv.x, uv.y, lod)) {
+  const uint4 r = query_variates(a, j, sample);
+  const int L = level_stochastic(t, a, lod, unit24(r.w));
+  const int W = t.level_w[L], H = t.level_h[L];
+  float x[2] = {__fsub_rn(__fmul_rn(uv.x, (float)W), 0.5f),
+                __fsub_rn(__fmul_rn(uv.y, (float)H), 0.5f)};
+  if (!(prepare_coords<2>(x) && isfinite(lod))) {
 #pragma unroll
     for (int c = 0; c < C; ++c) v[c] = 0.0f;
     tap = make_int4(0, 0, 0, -1);
     return;
   }
-  const uint64_t q = a.query_offset + (uint64_t)j;
-  const uint4 r = philox4x32_10(make_uint4((uint32_t)q, (uint32_t)(q >> 32), sample, 0u),
-                                a.key0, a.key1);
-  const int L = level_stochastic(t, a, lod, unit24(r.w));
-  const int W = t.level_w[L], H = t.level_h[L];
-  const float x = __fsub_rn(__fmul_rn(uv.x, (float)W), 0.5f);
-  const float y = __fsub_rn(__fmul_rn(uv.y, (float)H), 0.5f);
-  float fx, fy;
-  const int bx = axis_base(x, fx), by = axis_base(y, fy);
-  float wx[Fl::T], wy[Fl::T];
-  Fl::weights(fx, wx);
-  Fl::weights(fy, wy);
-  float Sx, Sy, sx, sy, u2;
-  const int kx = choose_tap<Fl::T>(unit24(r.x), wx, Sx, sx, u2);
-  const int ky = choose_tap<Fl::T>(a.reuse ? u2 : unit24(r.y), wy, Sy, sy, u2);
-  const int ix = bx + Fl::OFF0 + kx, iy = by + Fl::OFF0 + ky;
-  tap = make_int4(ix, iy, 0, L);
-  const int cx = min(max(ix, 0), W - 1), cy = min(max(iy, 0), H - 1);
+  const float u[2] = {unit24(r.x), unit24(r.y)};
+  int idx[2];
+  const float sigma = pick_taps<F, 2, REUSE>(x, u, idx);
+  tap = make_int4(idx[0], idx[1], 0, L);
+  const int cx = min(max(idx[0], 0), W - 1), cy = min(max(idx[1], 0), H - 1);
   TexelIO<FMT, C>::load(t.texels, t.level_off[L] + (int64_t)cy * W + cx, v);
-  if constexpr (!Fl::NONNEG) {
-    const float sigma = (sx * Sx) * (sy * Sy);
+  if constexpr (!Filter<F>::NONNEG) {
 #pragma unroll
     for (int c = 0; c < C; ++c) v[c] *= sigma;
   }
@@ -65,10 +55,11 @@ __device__ __forceinline__ void tex2d_det_level(const Tex2DView& t, int L, float
                                                 float* acc) {
   using Fl = Filter<F>;
   const int W = t.level_w[L], H = t.level_h[L];
-  const float x = __fsub_rn(__fmul_rn(uv.x, (float)W), 0.5f);
-  const float y = __fsub_rn(__fmul_rn(uv.y, (float)H), 0.5f);
+  float x[2] = {__fsub_rn(__fmul_rn(uv.x, (float)W), 0.5f),
+                __fsub_rn(__fmul_rn(uv.y, (float)H), 0.5f)};
+  if (!prepare_coords<2>(x)) return;
   float fx, fy;
-  const int bx = axis_base(x, fx) + Fl::OFF0, by = axis_base(y, fy) + Fl::OFF0;
+  const int bx = axis_base(x[0], fx) + Fl::OFF0, by = axis_base(x[1], fy) + Fl::OFF0;
   float wx[Fl::T], wy[Fl::T];
   Fl::weights(fx, wx);
   Fl::weights(fy, wy);
@@ -91,14 +82,14 @@ __device__ __forceinline__ void tex2d_det_level(const Tex2DView& t, int L, float
   }
 }
 
-template <int F, int FMT, int C>
+template <int F, int FMT, int C, bool REUSE>
 __global__ void __launch_bounds__(256) k_tex2d_stochastic(Tex2DView t, LookupArgs a) {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += stride) {
     float v[C];
     int4 tap;
     const int64_t j = query_slot(a, i);
-    tex2d_stochastic_one<F, FMT, C>(t, a, i, j, a.sample_index, v, tap);
+    tex2d_stochastic_one<F, FMT, C, REUSE>(t, a, i, j, a.sample_index, v, tap);
     store_out<C>(a.out, j, v);
     if (a.taps) reinterpret_cast<int4*>(a.taps)[j] = tap;
   }
@@ -113,7 +104,7 @@ __global__ void __launch_bounds__(256) k_tex2d_deterministic(Tex2DView t, Lookup
     float acc[C];
 #pragma unroll
     for (int c = 0; c < C; ++c) acc[c] = 0.0f;
-    if (finite3(uv.x, uv.y, lod)) {
+    if (isfinite(lod)) {
       if (a.lod == nullptr || t.levels <= 1) {
         tex2d_det_level<F, FMT, C>(t, 0, uv, 1.0f, acc);
       } else {
@@ -134,7 +125,7 @@ __global__ void __launch_bounds__(256) k_tex2d_deterministic(Tex2DView t, Lookup
   }
 }
 
-template <int F, int FMT, int C>
+template <int F, int FMT, int C, bool REUSE>
 __global__ void __launch_bounds__(256) k_tex2d_accumulate(Tex2DView t, LookupArgs a) {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += stride) {
@@ -144,7 +135,7 @@ __global__ void __launch_bounds__(256) k_tex2d_accumulate(Tex2DView t, LookupArg
     for (int k = 0; k < a.n_samples; ++k) {
       float v[C];
       int4 tap;
-      tex2d_stochastic_one<F, FMT, C>(t, a, i, i, a.sample_index + (uint32_t)k, v, tap);
+      tex2d_stochastic_one<F, FMT, C, REUSE>(t, a, i, i, a.sample_index + (uint32_t)k, v, tap);
 #pragma unroll
       for (int c = 0; c < C; ++c) {
         s[c] += (double)v[c];
@@ -173,44 +164,32 @@ __device__ __forceinline__ float dense_fetch(const Dense3DView& g, int ix, int i
     return __ldg(reinterpret_cast<const float*>(g.texels) + e);
 }
 
-template <int F, int FMT>
+template <int F, int FMT, bool REUSE>
 __device__ __forceinline__ float dense_stochastic_one(const Dense3DView& g, const LookupArgs& a,
                                                       int64_t i, int64_t j, uint32_t sample,
                                                       int4& tap) {
-  using Fl = Filter<F>;
-  const float px = __ldg(a.coords + 3 * i), py = __ldg(a.coords + 3 * i + 1),
-              pz = __ldg(a.coords + 3 * i + 2);
-  if (!finite3(px, py, pz)) {
+  float x[3] = {__ldg(a.coords + 3 * i), __ldg(a.coords + 3 * i + 1), __ldg(a.coords + 3 * i + 2)};
+  if (!prepare_coords<3>(x)) {
     tap = make_int4(0, 0, 0, -1);
     return g.background;
   }
-  const uint64_t q = a.query_offset + (uint64_t)j;
-  const uint4 r = philox4x32_10(make_uint4((uint32_t)q, (uint32_t)(q >> 32), sample, 0u),
-                                a.key0, a.key1);
-  float fx, fy, fz;
-  const int bx = axis_base(px, fx), by = axis_base(py, fy), bz = axis_base(pz, fz);
-  float w[Fl::T];
-  float Sx, Sy, Sz, sx, sy, sz, u2;
-  Fl::weights(fx, w);
-  const int kx = choose_tap<Fl::T>(unit24(r.x), w, Sx, sx, u2);
-  Fl::weights(fy, w);
-  const int ky = choose_tap<Fl::T>(a.reuse ? u2 : unit24(r.y), w, Sy, sy, u2);
-  Fl::weights(fz, w);
-  const int kz = choose_tap<Fl::T>(a.reuse ? u2 : unit24(r.z), w, Sz, sz, u2);
-  const int ix = bx + Fl::OFF0 + kx, iy = by + Fl::OFF0 + ky, iz = bz + Fl::OFF0 + kz;
-  tap = make_int4(ix, iy, iz, 0);
-  float t = dense_fetch<FMT>(g, ix, iy, iz);
-  if constexpr (!Fl::NONNEG) t *= ((sx * Sx) * (sy * Sy)) * (sz * Sz);
+  const uint4 r = query_variates(a, j, sample);
+  const float u[3] = {unit24(r.x), unit24(r.y), unit24(r.z)};
+  int idx[3];
+  const float sigma = pick_taps<F, 3, REUSE>(x, u, idx);
+  tap = make_int4(idx[0], idx[1], idx[2], 0);
+  float t = dense_fetch<FMT>(g, idx[0], idx[1], idx[2]);
+  if constexpr (!Filter<F>::NONNEG) t *= sigma;
   return t;
 }
 
-template <int F, int FMT>
+template <int F, int FMT, bool REUSE>
 __global__ void __launch_bounds__(256) k_dense_stochastic(Dense3DView g, LookupArgs a) {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += stride) {
     int4 tap;
     const int64_t j = query_slot(a, i);
-    a.out[j] = dense_stochastic_one<F, FMT>(g, a, i, j, a.sample_index, tap);
+    a.out[j] = dense_stochastic_one<F, FMT, REUSE>(g, a, i, j, a.sample_index, tap);
     if (a.taps) reinterpret_cast<int4*>(a.taps)[j] = tap;
   }
 }
@@ -220,13 +199,12 @@ __global__ void __launch_bounds__(256) k_dense_deterministic(Dense3DView g, Look
   using Fl = Filter<F>;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += stride) {
-    const float px = __ldg(a.coords + 3 * i), py = __ldg(a.coords + 3 * i + 1),
-                pz = __ldg(a.coords + 3 * i + 2);
+    float x[3] = {__ldg(a.coords + 3 * i), __ldg(a.coords + 3 * i + 1), __ldg(a.coords + 3 * i + 2)};
     float acc = g.background;
-    if (finite3(px, py, pz)) {
+    if (prepare_coords<3>(x)) {
       float fx, fy, fz;
-      const int bx = axis_base(px, fx) + Fl::OFF0, by = axis_base(py, fy) + Fl::OFF0,
-                bz = axis_base(pz, fz) + Fl::OFF0;
+      const int bx = axis_base(x[0], fx) + Fl::OFF0, by = axis_base(x[1], fy) + Fl::OFF0,
+                bz = axis_base(x[2], fz) + Fl::OFF0;
       float wx[Fl::T], wy[Fl::T], wz[Fl::T];
       Fl::weights(fx, wx);
       Fl::weights(fy, wy);
@@ -247,14 +225,14 @@ __global__ void __launch_bounds__(256) k_dense_deterministic(Dense3DView g, Look
   }
 }
 
-template <int F, int FMT>
+template <int F, int FMT, bool REUSE>
 __global__ void __launch_bounds__(256) k_dense_accumulate(Dense3DView g, LookupArgs a) {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += stride) {
     double s = 0.0, s2 = 0.0;
     for (int k = 0; k < a.n_samples; ++k) {
       int4 tap;
-      const double v = dense_stochastic_one<F, FMT>(g, a, i, i, a.sample_index + (uint32_t)k, tap);
+      const double v = dense_stochastic_one<F, FMT, REUSE>(g, a, i, i, a.sample_index + (uint32_t)k, tap);
       s += v;
       s2 += v * v;
     }
@@ -269,9 +247,15 @@ template <int F, int FMT, int C>
 static cudaError_t run_tex2d(Op op, const Tex2DView& t, const LookupArgs& a, cudaStream_t s) {
   const int threads = 256;
   const int blocks = grid_blocks(a.n, threads);
-  if (op == OP_STOCHASTIC) k_tex2d_stochastic<F, FMT, C><<<blocks, threads, 0, s>>>(t, a);
-  else if (op == OP_DETERMINISTIC) k_tex2d_deterministic<F, FMT, C><<<blocks, threads, 0, s>>>(t, a);
-  else k_tex2d_accumulate<F, FMT, C><<<blocks, threads, 0, s>>>(t, a);
+  if (op == OP_STOCHASTIC) {
+    if (a.reuse) k_tex2d_stochastic<F, FMT, C, true><<<blocks, threads, 0, s>>>(t, a);
+    else k_tex2d_stochastic<F, FMT, C, false><<<blocks, threads, 0, s>>>(t, a);
+  } else if (op == OP_DETERMINISTIC) {
+    k_tex2d_deterministic<F, FMT, C><<<blocks, threads, 0, s>>>(t, a);
+  } else {
+    if (a.reuse) k_tex2d_accumulate<F, FMT, C, true><<<blocks, threads, 0, s>>>(t, a);
+    else k_tex2d_accumulate<F, FMT, C, false><<<blocks, threads, 0, s>>>(t, a);
+  }
   return cudaGetLastError();
 }
 
@@ -311,9 +295,15 @@ template <int F, int FMT>
 static cudaError_t run_dense(Op op, const Dense3DView& g, const LookupArgs& a, cudaStream_t s) {
   const int threads = 256;
   const int blocks = grid_blocks(a.n, threads);
-  if (op == OP_STOCHASTIC) k_dense_stochastic<F, FMT><<<blocks, threads, 0, s>>>(g, a);
-  else if (op == OP_DETERMINISTIC) k_dense_deterministic<F, FMT><<<blocks, threads, 0, s>>>(g, a);
-  else k_dense_accumulate<F, FMT><<<blocks, threads, 0, s>>>(g, a);
+  if (op == OP_STOCHASTIC) {
+    if (a.reuse) k_dense_stochastic<F, FMT, true><<<blocks, threads, 0, s>>>(g, a);
+    else k_dense_stochastic<F, FMT, false><<<blocks, threads, 0, s>>>(g, a);
+  } else if (op == OP_DETERMINISTIC) {
+    k_dense_deterministic<F, FMT><<<blocks, threads, 0, s>>>(g, a);
+  } else {
+    if (a.reuse) k_dense_accumulate<F, FMT, true><<<blocks, threads, 0, s>>>(g, a);
+    else k_dense_accumulate<F, FMT, false><<<blocks, threads, 0, s>>>(g, a);
+  }
   return cudaGetLastError();
 }
 

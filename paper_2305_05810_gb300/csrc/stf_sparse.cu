@@ -293,38 +293,26 @@ __device__ __forceinline__ void stage_upper(const SparseDev& g, UpperSmem& su) {
   __syncthreads();
 }
 
-template <int F, int FMT>
+template <int F, int FMT, bool REUSE>
 __device__ __forceinline__ float sparse_stochastic_one(const SparseDev& g, const UpperSmem& su,
                                                        const LookupArgs& a, int64_t i, int64_t j,
                                                        uint32_t sample, int4& tap) {
-  using Fl = Filter<F>;
-  const float px = __ldg(a.coords + 3 * i), py = __ldg(a.coords + 3 * i + 1),
-              pz = __ldg(a.coords + 3 * i + 2);
-  if (!finite3(px, py, pz)) {
+  float x[3] = {__ldg(a.coords + 3 * i), __ldg(a.coords + 3 * i + 1), __ldg(a.coords + 3 * i + 2)};
+  if (!prepare_coords<3>(x)) {
     tap = make_int4(0, 0, 0, -1);
     return g.background;
   }
-  const uint64_t q = a.query_offset + (uint64_t)j;
-  const uint4 r = philox4x32_10(make_uint4((uint32_t)q, (uint32_t)(q >> 32), sample, 0u),
-                                a.key0, a.key1);
-  float fx, fy, fz;
-  const int bx = axis_base(px, fx), by = axis_base(py, fy), bz = axis_base(pz, fz);
-  float w[Fl::T];
-  float Sx, Sy, Sz, sx, sy, sz, u2;
-  Fl::weights(fx, w);
-  const int kx = choose_tap<Fl::T>(unit24(r.x), w, Sx, sx, u2);
-  Fl::weights(fy, w);
-  const int ky = choose_tap<Fl::T>(a.reuse ? u2 : unit24(r.y), w, Sy, sy, u2);
-  Fl::weights(fz, w);
-  const int kz = choose_tap<Fl::T>(a.reuse ? u2 : unit24(r.z), w, Sz, sz, u2);
-  const int ix = bx + Fl::OFF0 + kx, iy = by + Fl::OFF0 + ky, iz = bz + Fl::OFF0 + kz;
-  tap = make_int4(ix, iy, iz, 0);
-  float t = sparse_value<FMT>(g, sparse_leaf(g, su, ix, iy, iz), ix, iy, iz);
-  if constexpr (!Fl::NONNEG) t *= ((sx * Sx) * (sy * Sy)) * (sz * Sz);
+  const uint4 r = query_variates(a, j, sample);
+  const float u[3] = {unit24(r.x), unit24(r.y), unit24(r.z)};
+  int idx[3];
+  const float sigma = pick_taps<F, 3, REUSE>(x, u, idx);
+  tap = make_int4(idx[0], idx[1], idx[2], 0);
+  float t = sparse_value<FMT>(g, sparse_leaf(g, su, idx[0], idx[1], idx[2]), idx[0], idx[1], idx[2]);
+  if constexpr (!Filter<F>::NONNEG) t *= sigma;
   return t;
 }
 
-template <int F, int FMT>
+template <int F, int FMT, bool REUSE>
 __global__ void __launch_bounds__(256) k_sparse_stochastic(SparseDev g, LookupArgs a) {
   __shared__ UpperSmem su;
   stage_upper(g, su);
@@ -332,7 +320,7 @@ __global__ void __launch_bounds__(256) k_sparse_stochastic(SparseDev g, LookupAr
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += stride) {
     int4 tap;
     const int64_t j = query_slot(a, i);
-    a.out[j] = sparse_stochastic_one<F, FMT>(g, su, a, i, j, a.sample_index, tap);
+    a.out[j] = sparse_stochastic_one<F, FMT, REUSE>(g, su, a, i, j, a.sample_index, tap);
     if (a.taps) reinterpret_cast<int4*>(a.taps)[j] = tap;
   }
 }
@@ -346,13 +334,12 @@ __global__ void __launch_bounds__(256) k_sparse_deterministic(SparseDev g, Looku
   stage_upper(g, su);
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += stride) {
-    const float px = __ldg(a.coords + 3 * i), py = __ldg(a.coords + 3 * i + 1),
-                pz = __ldg(a.coords + 3 * i + 2);
+    float x[3] = {__ldg(a.coords + 3 * i), __ldg(a.coords + 3 * i + 1), __ldg(a.coords + 3 * i + 2)};
     float acc = g.background;
-    if (finite3(px, py, pz)) {
+    if (prepare_coords<3>(x)) {
       float fx, fy, fz;
-      const int bx = axis_base(px, fx) + Fl::OFF0, by = axis_base(py, fy) + Fl::OFF0,
-                bz = axis_base(pz, fz) + Fl::OFF0;
+      const int bx = axis_base(x[0], fx) + Fl::OFF0, by = axis_base(x[1], fy) + Fl::OFF0,
+                bz = axis_base(x[2], fz) + Fl::OFF0;
       float wx[Fl::T], wy[Fl::T], wz[Fl::T];
       Fl::weights(fx, wx);
       Fl::weights(fy, wy);
@@ -389,7 +376,7 @@ __global__ void __launch_bounds__(256) k_sparse_deterministic(SparseDev g, Looku
   }
 }
 
-template <int F, int FMT>
+template <int F, int FMT, bool REUSE>
 __global__ void __launch_bounds__(256) k_sparse_accumulate(SparseDev g, LookupArgs a) {
   __shared__ UpperSmem su;
   stage_upper(g, su);
@@ -398,7 +385,7 @@ __global__ void __launch_bounds__(256) k_sparse_accumulate(SparseDev g, LookupAr
     double s = 0.0, s2 = 0.0;
     for (int k = 0; k < a.n_samples; ++k) {
       int4 tap;
-      const double v = sparse_stochastic_one<F, FMT>(g, su, a, i, i, a.sample_index + (uint32_t)k, tap);
+      const double v = sparse_stochastic_one<F, FMT, REUSE>(g, su, a, i, i, a.sample_index + (uint32_t)k, tap);
       s += v;
       s2 += v * v;
     }
@@ -411,9 +398,15 @@ template <int F, int FMT>
 static cudaError_t run_sparse(Op op, const SparseDev& g, const LookupArgs& a, cudaStream_t s) {
   const int threads = 256;
   const int blocks = grid_blocks(a.n, threads);
-  if (op == OP_STOCHASTIC) k_sparse_stochastic<F, FMT><<<blocks, threads, 0, s>>>(g, a);
-  else if (op == OP_DETERMINISTIC) k_sparse_deterministic<F, FMT><<<blocks, threads, 0, s>>>(g, a);
-  else k_sparse_accumulate<F, FMT><<<blocks, threads, 0, s>>>(g, a);
+  if (op == OP_STOCHASTIC) {
+    if (a.reuse) k_sparse_stochastic<F, FMT, true><<<blocks, threads, 0, s>>>(g, a);
+    else k_sparse_stochastic<F, FMT, false><<<blocks, threads, 0, s>>>(g, a);
+  } else if (op == OP_DETERMINISTIC) {
+    k_sparse_deterministic<F, FMT><<<blocks, threads, 0, s>>>(g, a);
+  } else {
+    if (a.reuse) k_sparse_accumulate<F, FMT, true><<<blocks, threads, 0, s>>>(g, a);
+    else k_sparse_accumulate<F, FMT, false><<<blocks, threads, 0, s>>>(g, a);
+  }
   return cudaGetLastError();
 }
 
