@@ -163,6 +163,31 @@ stf_status stf_lookup_accumulate(stf_texture tex, const stf_lookup_params* param
                                  int32_t n_samples, double* d_sum, double* d_sumsq,
                                  void* stream);
 
+/* Largest n accepted by stf_lookup_batch_binned_noalloc. */
+#define STF_NOALLOC_MAX_QUERIES (1 << 20)
+
+/* Allocation-free Morton-binned stochastic lookup.  Same arguments and results as
+ * stf_lookup_batch with params->bin_queries = 1 (bin_queries itself is ignored),
+ * but the binning scratch lives in a fixed array inside the library's device
+ * image (16.5 MiB, held by every GPU that loads the library until the process
+ * exits) instead of device memory allocated per call.  It is meant for callers
+ * that must not have the library allocate device memory: processes that reserve
+ * their whole device-memory budget up front with their own allocator, and
+ * callers that cannot accept the synchronisation an allocation may imply.  The
+ * paper has no counterpart; this is an integration entry point.
+ *   - n above STF_NOALLOC_MAX_QUERIES returns STF_ERR_INVALID_ARGUMENT.
+ *   - The first call on a device looks up the array's device address (once per
+ *     device, with that device current); make that first call before any stream
+ *     capture.
+ *   - Every call shares the one array, which keeps the last call's contents (the
+ *     bin counts are cleared at the start of each call).  Calls whose work
+ *     overlaps on the GPU (different streams, or different host threads) race on
+ *     it: serialise them, e.g. on one stream.
+ *   - It calls no cudaMalloc, cudaFree or allocating library routine. */
+stf_status stf_lookup_batch_binned_noalloc(stf_texture tex, const stf_lookup_params* params,
+                                           const float* d_coords, const float* d_lod, int64_t n,
+                                           float* d_out, int32_t* d_taps, void* stream);
+
 /* Bytes of device memory the texture holds (texels, tree nodes, scratch). */
 stf_status stf_texture_bytes(stf_texture tex, int64_t* out_bytes);
 

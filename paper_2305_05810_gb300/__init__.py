@@ -13,6 +13,7 @@ from . import build as _build
 __all__ = [
     "StfError", "TextureDesc", "LookupParams", "stf_create_texture", "stf_destroy",
     "stf_lookup_batch", "stf_lookup_batch_deterministic", "stf_lookup_accumulate",
+    "stf_lookup_batch_binned_noalloc",
     "stf_texture_bytes", "stf_synchronize", "stf_last_error", "stf_version", "Texture",
     "KIND_TEX2D", "KIND_DENSE3D", "KIND_SPARSE3D", "FMT_F32", "FMT_F16", "FMT_E4M3_SCALED",
     "FILTER_LINEAR", "FILTER_BSPLINE3", "FILTER_CATMULL_ROM", "LEVEL_NEAREST",
@@ -24,6 +25,7 @@ FMT_F32, FMT_F16, FMT_E4M3_SCALED = 0, 1, 2
 FILTER_LINEAR, FILTER_BSPLINE3, FILTER_CATMULL_ROM = 0, 1, 2
 FILTERS = {"linear": FILTER_LINEAR, "bspline3": FILTER_BSPLINE3, "catmull_rom": FILTER_CATMULL_ROM}
 LEVEL_NEAREST, LEVEL_STOCHASTIC = 0, 1
+STF_NOALLOC_MAX_QUERIES = 1 << 20   # include/stf.h
 
 STATUS = {0: "STF_OK", 1: "STF_ERR_INVALID_ARGUMENT", 2: "STF_ERR_INVALID_HANDLE",
           3: "STF_ERR_OUT_OF_MEMORY", 4: "STF_ERR_UNSUPPORTED", 5: "STF_ERR_CUDA",
@@ -75,6 +77,7 @@ def load(build_if_missing=True):
     lib.stf_destroy.argtypes = [VP]
     lib.stf_lookup_batch.argtypes = [VP, P(LookupParams), VP, VP, I64, VP, VP, VP]
     lib.stf_lookup_batch_deterministic.argtypes = [VP, P(LookupParams), VP, VP, I64, VP, VP]
+    lib.stf_lookup_batch_binned_noalloc.argtypes = [VP, P(LookupParams), VP, VP, I64, VP, VP, VP]
     lib.stf_lookup_accumulate.argtypes = [VP, P(LookupParams), VP, VP, I64, I32, VP, VP, VP]
     lib.stf_texture_bytes.argtypes = [VP, P(I64)]
     lib.stf_synchronize.argtypes = [VP, VP]
@@ -85,7 +88,7 @@ def load(build_if_missing=True):
     lib.stf_debug_fail_allocation.restype = None
     for f in ("stf_create_texture", "stf_destroy", "stf_lookup_batch",
               "stf_lookup_batch_deterministic", "stf_lookup_accumulate", "stf_texture_bytes",
-              "stf_synchronize"):
+              "stf_synchronize", "stf_lookup_batch_binned_noalloc"):
         getattr(lib, f).restype = I32
     _lib = lib
     return lib
@@ -135,6 +138,11 @@ def stf_destroy(tex):
 def stf_lookup_batch(tex, params, coords, lod, n, out, taps=None, stream=None):
     _check(load().stf_lookup_batch(tex, ctypes.byref(params), _ptr(coords), _ptr(lod), int(n),
                                    _ptr(out), _ptr(taps), _stream(stream)))
+
+
+def stf_lookup_batch_binned_noalloc(tex, params, coords, lod, n, out, taps=None, stream=None):
+    _check(load().stf_lookup_batch_binned_noalloc(tex, ctypes.byref(params), _ptr(coords), _ptr(lod),
+                                                  int(n), _ptr(out), _ptr(taps), _stream(stream)))
 
 
 def stf_lookup_batch_deterministic(tex, params, coords, lod, n, out, stream=None):

@@ -214,3 +214,86 @@ stf_status lookup_binned(stf_texture t, int filter, const LookupArgs& a0, cudaSt
 }
 
 }  // namespace stf
+
+// ---------------------------------------------------------------- allocation-free variant
+//
+// stf_lookup_batch_binned_noalloc: the binned stochastic lookup above, with its
+// scratch in a fixed device array that is part of the library image instead of
+// the stream-ordered pool.  For callers that must not allocate device memory from
+// inside the library: processes that reserve their whole device-memory budget up
+// front with their own allocator (render engines, serving processes), where a
+// library-side allocation could fail or fragment that budget, and callers that
+// cannot afford the device-wide synchronisation cudaMalloc/cudaFree may imply.
+
+namespace {
+
+constexpr int64_t kNoAllocMaxQueries = STF_NOALLOC_MAX_QUERIES;
+// [histogram | cursors] (2 x 65536 words) | permutation (max queries words) |
+// binned coordinates, 3 floats per query for 3D, or 2 floats + lod for 2D.
+constexpr size_t kNoAllocHistBytes = sizeof(uint32_t) * 2 * stf::kBins2D;
+constexpr size_t kNoAllocPermBytes = sizeof(uint32_t) * kNoAllocMaxQueries;
+constexpr size_t kNoAllocCoordBytes = sizeof(float) * 3 * kNoAllocMaxQueries;
+constexpr size_t kNoAllocBytes = kNoAllocHistBytes + kNoAllocPermBytes + kNoAllocCoordBytes;
+
+// Held by every GPU that loads the library, until the process exits.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+std::mutex g_noalloc_mutex;
+void* g_noalloc_ptr[64];   // device address of g_noalloc_scratch, per device
+
+// Device address of the scratch array on the current device (looked up once per
+// device; the host-side name of the array is not a device address).
+stf_status noalloc_scratch(void** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return stf::fail_cuda(e, "current device");
+  std::lock_guard<std::mutex> lk(g_noalloc_mutex);
+  if (!g_noalloc_ptr[dev & 63]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return stf::fail_cuda(e, "static scratch address");
+    g_noalloc_ptr[dev & 63] = p;
+  }
+  *out = g_noalloc_ptr[dev & 63];
+  return STF_OK;
+}
+
+}  // namespace
+
+extern "C" stf_status stf_lookup_batch_binned_noalloc(stf_texture t, const stf_lookup_params* p,
+                                                      const float* coords, const float* lod,
+                                                      int64_t n, float* out, int32_t* taps,
+                                                      void* stream) {
+  using namespace stf;
+  stf_status st = check_lookup(t, p, coords, lod, n, out);
+  if (st != STF_OK || n == 0) return st;
+  if (n > kNoAllocMaxQueries)
+    return fail(STF_ERR_INVALID_ARGUMENT,
+                "n = %lld exceeds the allocation-free limit of %lld queries per call",
+                (long long)n, (long long)kNoAllocMaxQueries);
+  if (taps && (uintptr_t)taps % 16) return fail(STF_ERR_INVALID_ARGUMENT, "taps not 16-byte aligned");
+  void* scratch = nullptr;
+  st = noalloc_scratch(&scratch);
+  if (st != STF_OK) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  const BinSpec b = bin_spec(t);
+  const int nbins = b.dims == 2 ? kBins2D : kBins3D;
+  char* base = (char*)scratch;
+  uint32_t* hist = (uint32_t*)base;
+  uint32_t* cursor = hist + nbins;
+  uint32_t* perm = (uint32_t*)(base + kNoAllocHistBytes);
+  float* bcoords = (float*)(base + kNoAllocHistBytes + kNoAllocPermBytes);
+  float* blod = (b.dims == 2 && lod) ? bcoords + 2 * kNoAllocMaxQueries : nullptr;
+  cudaError_t e = cudaMemsetAsync(hist, 0, sizeof(uint32_t) * nbins, s);   // counts start at zero
+  const int blocks = grid_blocks(n, 256);
+  if (e == cudaSuccess) {
+    k_bin_hist<<<blocks, 256, 0, s>>>(b, coords, n, hist);
+    k_bin_scan<<<1, 1024, 0, s>>>(hist, cursor, nbins);
+    k_bin_scatter<<<blocks, 256, 0, s>>>(b, coords, lod, n, cursor, perm, bcoords, blod);
+    e = cudaGetLastError();
+  }
+  if (e != cudaSuccess) return fail_cuda(e, "binning launch");
+  LookupArgs a = make_args(p, bcoords, blod, n, out, taps);
+  a.perm = perm;
+  return dispatch(OP_STOCHASTIC, t, p->filter, a, s);
+}
