@@ -352,6 +352,16 @@ def run_ours(args):
             variants += [("stochastic_linear", stochastic("linear")),
                          ("deterministic_linear", deterministic("linear"))]
         variants += [("stochastic_binned", stochastic(bin_queries=True))]
+        # the same queries in a seeded random order (incoherent rays): where binning pays
+        g = torch.Generator(device=dev)
+        g.manual_seed(7)
+        shuffled = coords[torch.randperm(n, device=dev, generator=g)].contiguous()
+        pshuf = stf.make_params(filt, seed=2024)
+        pshuf_b = stf.make_params(filt, seed=2024, bin_queries=True)
+        variants += [("stochastic_shuffled", lambda: stf.stf_lookup_batch(
+                          tex.handle, pshuf, shuffled, None, n, out, None, stream)),
+                     ("stochastic_shuffled_binned", lambda: stf.stf_lookup_batch(
+                          tex.handle, pshuf_b, shuffled, None, n, out, None, stream))]
         for name, fn in variants:
             try:
                 p2, t2 = time_steps(torch, fn, max(3, args.steps // 2), 2, stream)

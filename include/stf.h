@@ -169,7 +169,7 @@ stf_status stf_lookup_accumulate(stf_texture tex, const stf_lookup_params* param
 /* Allocation-free Morton-binned stochastic lookup.  Same arguments and results as
  * stf_lookup_batch with params->bin_queries = 1 (bin_queries itself is ignored),
  * but the binning scratch lives in a fixed array inside the library's device
- * image (16.5 MiB, held by every GPU that loads the library until the process
+ * image (16 MiB plus 8 KiB, held by every GPU that loads the library until the process
  * exits) instead of device memory allocated per call.  It is meant for callers
  * that must not have the library allocate device memory: processes that reserve
  * their whole device-memory budget up front with their own allocator, and

@@ -1,0 +1,238 @@
+"""Continuous-batching request loop over the lookup library.
+
+Requests (a batch of query coordinates against one device-resident texture, a
+filter, stochastic or deterministic) arrive over time.  The server keeps a fixed
+set of slots, each a CUDA stream.  A waiting request is admitted when a slot is
+free and its device footprint (coordinates, levels of detail, results) fits in the
+memory budget next to the requests already admitted; requests that arrive while
+others run are admitted as slots and memory free up, and the work of all admitted
+requests overlaps on the GPU.  Each request runs as a sequence of chunks (host to
+device copy, one library call, device to host copy) on its slot's stream; chunks
+pass query_offset so the random variates stay keyed on the request-local query
+index: a request's result is the same whether it runs alone or in any mix.
+
+The loop itself (admission, budget, chunking, completion) lives in ``Scheduler``,
+which talks to the device through a small backend interface so that it can be
+tested without a GPU; ``TorchBackend`` is the real one.
+"""
+import collections
+import math
+import time
+
+import paper_2305_05810_gb300 as stf
+
+
+class BudgetError(RuntimeError):
+    """A request can never fit in the memory budget (STF_ERR_BUDGET)."""
+    status = 7
+
+
+class Request:
+    """One lookup request.  ``coords`` is a host tensor (pinned for overlap),
+    n x 2 for 2D textures and n x 3 for 3D grids; ``lod`` is optional (2D)."""
+
+    def __init__(self, rid, texture, coords, lod=None, *, filter="bspline3", stochastic=True,
+                 seed=0, level_mode=stf.LEVEL_STOCHASTIC, arrival=0.0):
+        self.rid = rid
+        self.texture = texture
+        self.coords = coords
+        self.lod = lod
+        self.filter = filter
+        self.stochastic = stochastic
+        self.seed = seed
+        self.level_mode = level_mode
+        self.arrival = arrival
+        self.n = int(coords.shape[0])
+        self.result = None
+        self.t_admit = None
+        self.t_done = None
+
+    def device_bytes(self, channels):
+        per = self.coords.shape[1] * 4 + channels * 4 + (4 if self.lod is not None else 0)
+        return self.n * per
+
+    @property
+    def latency(self):
+        return None if self.t_done is None else self.t_done - self.arrival
+
+
+class Scheduler:
+    """Admission, chunking and completion; the device side is the backend."""
+
+    def __init__(self, backend, n_slots=8, budget_bytes=16 << 30, chunk_queries=1 << 20,
+                 max_chunks_in_flight=2, clock=time.perf_counter):
+        self.backend = backend
+        self.n_slots = n_slots
+        self.budget = int(budget_bytes)
+        self.chunk = int(chunk_queries)
+        self.depth = max_chunks_in_flight
+        self.clock = clock
+        self.waiting = collections.deque()
+        self.free_slots = collections.deque(range(n_slots))
+        self.active = {}            # slot -> job
+        self.in_use = 0
+        self.done = []
+        self.rejected = []
+        self.peak_in_use = 0
+        self.peak_active = 0
+
+    def submit(self, req):
+        need = req.device_bytes(self.backend.channels(req.texture))
+        if need > self.budget:
+            self.rejected.append(req)
+            raise BudgetError("request %r needs %d bytes, budget is %d" % (req.rid, need, self.budget))
+        self.waiting.append(req)
+
+    def _admit(self):
+        while self.waiting and self.free_slots:
+            req = self.waiting[0]
+            need = req.device_bytes(self.backend.channels(req.texture))
+            if self.in_use + need > self.budget:
+                return                                  # FIFO: wait for memory
+            self.waiting.popleft()
+            slot = self.free_slots.popleft()
+            self.in_use += need
+            self.peak_in_use = max(self.peak_in_use, self.in_use)
+            req.t_admit = self.clock()
+            job = {"req": req, "slot": slot, "bytes": need, "next": 0, "inflight": collections.deque(),
+                   "state": self.backend.begin(req, slot)}
+            self.active[slot] = job
+            self.peak_active = max(self.peak_active, len(self.active))
+
+    def _issue(self):
+        for slot, job in self.active.items():
+            req = job["req"]
+            while job["next"] < req.n and len(job["inflight"]) < self.depth:
+                a = job["next"]
+                b = min(req.n, a + self.chunk)
+                job["inflight"].append(self.backend.launch_chunk(job["state"], req, slot, a, b))
+                job["next"] = b
+
+    def _retire(self):
+        finished = []
+        for slot, job in self.active.items():
+            q = job["inflight"]
+            while q and self.backend.chunk_done(q[0]):
+                q.popleft()
+            if not q and job["next"] >= job["req"].n:
+                finished.append(slot)
+        for slot in finished:
+            job = self.active.pop(slot)
+            req = job["req"]
+            req.result = self.backend.finish(job["state"], req)
+            req.t_done = self.clock()
+            self.in_use -= job["bytes"]
+            self.free_slots.append(slot)
+            self.done.append(req)
+
+    def step(self):
+        self._retire()
+        self._admit()
+        self._issue()
+
+    def idle(self):
+        return not self.waiting and not self.active
+
+    def run(self, requests, realtime=True):
+        """Serve requests (sorted by arrival).  With realtime, arrivals are released
+        at their arrival times relative to the start; latencies are measured from
+        those times."""
+        pending = collections.deque(sorted(requests, key=lambda r: r.arrival))
+        t0 = self.clock()
+        for r in pending:
+            r.arrival = t0 + r.arrival if realtime else t0
+        while pending or not self.idle():
+            now = self.clock()
+            while pending and pending[0].arrival <= now:
+                r = pending.popleft()
+                try:
+                    self.submit(r)
+                except BudgetError:
+                    pass
+            self.step()
+            if self.idle() and pending:
+                wait = pending[0].arrival - self.clock()
+                if wait > 0:
+                    time.sleep(min(wait, 0.001))
+        return self.done
+
+
+class TorchBackend:
+    """Device side of the scheduler: torch streams, pinned host buffers, the C ABI."""
+
+    def __init__(self, textures, n_slots=8, device=None):
+        import torch
+        self.torch = torch
+        self.textures = textures                       # key -> stf.Texture
+        self.device = device or torch.device("cuda", torch.cuda.current_device())
+        self.streams = [torch.cuda.Stream(device=self.device) for _ in range(n_slots)]
+
+    def channels(self, key):
+        return self.textures[key].channels
+
+    def begin(self, req, slot):
+        torch = self.torch
+        T = self.textures[req.texture]
+        with torch.cuda.stream(self.streams[slot]):
+            d_coords = torch.empty(tuple(req.coords.shape), dtype=torch.float32, device=self.device)
+            d_lod = None if req.lod is None else torch.empty((req.n,), dtype=torch.float32, device=self.device)
+            d_out = torch.empty((req.n, T.channels), dtype=torch.float32, device=self.device)
+        h_out = torch.empty((req.n, T.channels), dtype=torch.float32, pin_memory=True)
+        params = stf.make_params(req.filter, seed=req.seed, level_mode=req.level_mode)
+        return {"T": T, "d_coords": d_coords, "d_lod": d_lod, "d_out": d_out, "h_out": h_out,
+                "params": params}
+
+    def launch_chunk(self, st, req, slot, a, b):
+        torch = self.torch
+        s = self.streams[slot]
+        with torch.cuda.stream(s):
+            st["d_coords"][a:b].copy_(req.coords[a:b], non_blocking=True)
+            lod = None
+            if req.lod is not None:
+                st["d_lod"][a:b].copy_(req.lod[a:b], non_blocking=True)
+                lod = st["d_lod"][a:b]
+            p = st["params"]
+            p.query_offset = a
+            if req.stochastic:
+                stf.stf_lookup_batch(st["T"].handle, p, st["d_coords"][a:b], lod, b - a,
+                                     st["d_out"][a:b], None, s)
+            else:
+                stf.stf_lookup_batch_deterministic(st["T"].handle, p, st["d_coords"][a:b], lod,
+                                                   b - a, st["d_out"][a:b], s)
+            st["h_out"][a:b].copy_(st["d_out"][a:b], non_blocking=True)
+            ev = torch.cuda.Event()
+            ev.record(s)
+        return ev
+
+    def chunk_done(self, ev):
+        return ev.query()
+
+    def finish(self, st, req):
+        return st["h_out"]
+
+
+def poisson_requests(n, rate_per_s, sizes, make, seed=6):
+    """n requests with exponential inter-arrival times (Poisson process of the given
+    rate) and log-uniform sizes in [sizes[0], sizes[1]]; make(i, size, rng) builds
+    each Request (its arrival is filled in here)."""
+    import numpy as np
+    rng = np.random.default_rng(seed)
+    t = 0.0
+    out = []
+    lo, hi = math.log(sizes[0]), math.log(sizes[1])
+    for i in range(n):
+        t += rng.exponential(1.0 / rate_per_s)
+        size = int(round(math.exp(rng.uniform(lo, hi))))
+        r = make(i, size, rng)
+        r.arrival = t
+        out.append(r)
+    return out
+
+
+def latency_summary(done):
+    lat = sorted(r.latency for r in done)
+    if not lat:
+        return {}
+    pick = lambda p: lat[min(len(lat) - 1, int(round(p / 100.0 * (len(lat) - 1))))]
+    return {"p50_ms": 1e3 * pick(50), "p99_ms": 1e3 * pick(99), "mean_ms": 1e3 * sum(lat) / len(lat),
+            "requests": len(lat)}

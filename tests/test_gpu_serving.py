@@ -1,0 +1,82 @@
+"""Serving loop on the GPU: mixed requests (2D, dense and sparse textures; stochastic
+and deterministic; uneven sizes) admitted into overlapping slots under a memory
+budget.  Each request's result in the mix must equal the same request run alone
+through one direct library call (bit-identical: the variates are keyed on the
+request-local query index, whatever the chunking or the mix)."""
+import numpy as np
+import pytest
+import torch
+
+import paper_2305_05810_gb300 as stf
+import synth
+from paper_2305_05810_gb300 import serving
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def textures():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    stf.load()
+    tex2d = stf.Texture(stf.KIND_TEX2D, synth.texture2d(256, 256, 4, seed=1), dims=(256, 256, 1),
+                        channels=4, mip_levels=9, generate_mips=True)
+    dense = stf.Texture(stf.KIND_DENSE3D, synth.dense_density(n=64, seed=3, period=12.0),
+                        dims=(64, 64, 64), fmt=stf.FMT_F16)
+    origins, values = synth.sparse_cloud(domain=512, seed=4)
+    sparse = stf.Texture(stf.KIND_SPARSE3D, values, fmt=stf.FMT_E4M3_SCALED, leaf_origins=origins)
+    return {"tex2d": tex2d, "dense": dense, "sparse": sparse}
+
+
+def _make(textures):
+    pools = {
+        "tex2d": torch.from_numpy(synth.uv_queries(1 << 20, seed=2)),
+        "dense": torch.from_numpy(synth.camera_queries(W=256, H=256, steps=16, centre=(32, 32, 32),
+                                                       radius=96, half_span=56, seed=3)),
+        "sparse": torch.from_numpy(synth.camera_queries(W=256, H=256, steps=16, centre=(256, 256, 256),
+                                                        radius=768, half_span=444, seed=4)),
+    }
+    lods = torch.from_numpy(synth.lods(1 << 20, seed=9, lo=0, hi=8))
+    keys = list(textures)
+
+    def make(i, size, rng):
+        key = keys[i % len(keys)]
+        pool = pools[key]
+        start = int(rng.integers(0, pool.shape[0] - size))
+        coords = pool[start:start + size].clone().pin_memory()
+        lod = lods[:size].clone().pin_memory() if key == "tex2d" and i % 2 else None
+        filt = ("linear", "bspline3", "catmull_rom")[i % 3]
+        return serving.Request(i, key, coords, lod, filter=filt, stochastic=(i % 4 != 3), seed=100 + i)
+    return make
+
+
+def test_each_result_is_the_same_alone_and_in_the_mix(textures):
+    make = _make(textures)
+    reqs = serving.poisson_requests(48, 2000.0, (1000, 1 << 19), make, seed=6)
+    backend = serving.TorchBackend(textures, n_slots=6)
+    sched = serving.Scheduler(backend, n_slots=6, budget_bytes=64 << 20, chunk_queries=1 << 16)
+    done = sched.run(reqs)
+    assert len(done) == len(reqs) and sched.peak_active >= 2
+    assert sched.peak_in_use <= 64 << 20
+    for r in reqs:
+        T = textures[r.texture]
+        d = r.coords.cuda()
+        lod = None if r.lod is None else r.lod.cuda()
+        alone = torch.empty((r.n, T.channels), dtype=torch.float32, device="cuda")
+        p = stf.make_params(r.filter, seed=r.seed, level_mode=r.level_mode)
+        if r.stochastic:
+            stf.stf_lookup_batch(T.handle, p, d, lod, r.n, alone)
+        else:
+            stf.stf_lookup_batch_deterministic(T.handle, p, d, lod, r.n, alone)
+        torch.cuda.synchronize()
+        assert torch.equal(alone.cpu(), r.result), r.rid
+    s = serving.latency_summary(done)
+    assert s["p99_ms"] >= s["p50_ms"] > 0
+
+
+def test_request_over_budget_is_rejected_on_gpu(textures):
+    backend = serving.TorchBackend(textures, n_slots=2)
+    sched = serving.Scheduler(backend, n_slots=2, budget_bytes=1 << 20)
+    big = serving.Request(0, "dense", torch.zeros((1 << 17, 3)))
+    with pytest.raises(serving.BudgetError):
+        sched.submit(big)
