@@ -36,6 +36,7 @@ ALGO_BYTES = {  # algorithmic bytes per lookup: query in + texel(s) + result out
     ("dense", "stochastic"): 12 + 2 + 4,
     ("sparse", "stochastic"): 12 + 4 + 4,
     ("sparse_e4m3", "stochastic"): 12 + 1 + 4 + 4,
+    ("neural", "stochastic"): 12 + 16 + 28,
     ("dense", "deterministic", "bspline3"): 12 + 64 * 2 + 4,
     ("dense", "deterministic", "linear"): 12 + 8 * 2 + 4,
     ("tex2d", "stochastic"): 8 + 16 + 16,
@@ -50,8 +51,11 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="dense", choices=["dense", "tex2d", "sparse", "sparse_e4m3"])
-    ap.add_argument("--filter", default="bspline3", choices=["linear", "bspline3", "catmull_rom"])
+    ap.add_argument("--workload", default="dense",
+                    choices=["dense", "tex2d", "sparse", "sparse_e4m3", "neural"])
+    ap.add_argument("--train-steps", type=int, default=400)
+    ap.add_argument("--filter", default=None, choices=["linear", "bspline3", "catmull_rom"],
+                    help="default: bspline3 (linear for the neural workload)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--quick", action="store_true", help="skip the extra variants")
     return ap.parse_args()
@@ -66,6 +70,16 @@ def make_workload(name):
         q = synth.camera_queries(**synth.C2_RAYS)
         desc = "dense 256^3 FP16 fractal-noise density (30% non-zero), 1920x1080 rays x 16 steps"
         return dict(name=name, values=vals, coords=q, dims=(256, 256, 256), channels=1, desc=desc)
+    if name == "neural":
+        size, nlat, nlev = 4096, 4, 13
+        latents, params = synth.neural_init(size, nlat, seed=5)
+        pyr = synth.box_levels(synth.material(size, seed=5), nlev)
+        n = 1 << 24
+        desc = ("neural 4096^2 RGB+normal+roughness, 4 FP16 latent levels x 8 ch + MLP 8-64-64-7, "
+                "fallback FP16 mips; 16,777,216 uv queries, lod ~ U[0, 4)")
+        return dict(name=name, size=size, nlat=nlat, nlev=nlev, latents=latents, params=params,
+                    pyramid=pyr, coords=synth.uv_queries(n, seed=2), lod=synth.lods(n, seed=9),
+                    channels=7, desc=desc)
     if name.startswith("sparse"):
         origins, values = synth.sparse_cloud(domain=2048, seed=4)
         q = synth.camera_queries(**synth.C3_RAYS)
@@ -81,7 +95,17 @@ def make_workload(name):
     return dict(name=name, values=tex, coords=uv, dims=(256, 256, 1), channels=4, desc=desc)
 
 
-def make_texture(stf, w, fmt=None):
+def make_texture(stf, w, fmt=None, train_steps=400):
+    if w["name"] == "neural":
+        import torch
+        pyr = w["pyramid"]
+        fb = np.concatenate([p.reshape(-1, 7) for p in pyr[w["nlat"]:]])
+        T = stf.NeuralTexture(w["size"], w["size"], w["nlat"], w["nlev"], w["latents"], w["params"], fb)
+        target = torch.from_numpy(np.concatenate([p.reshape(-1, 7) for p in pyr[:w["nlat"]]])).cuda()
+        losses = T.train(target, steps=train_steps, batch=1 << 16, lr_latent=3e-2, lr_params=3e-3, seed=11)
+        w["train_loss"] = (float(losses[0].item()), float(losses[-1].item())) if train_steps else None
+        del target
+        return T
     if w["name"] == "dense":
         return stf.Texture(stf.KIND_DENSE3D, w["values"], dims=w["dims"],
                            fmt=stf.FMT_F16 if fmt is None else fmt)
@@ -221,6 +245,13 @@ def ncu_traffic(key):
     return None
 
 
+def bf16_peak():
+    try:
+        return float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["bf16_tflops"])
+    except (OSError, ValueError, KeyError):
+        return 1900.0
+
+
 def peaks():
     try:
         d = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -253,6 +284,18 @@ def cpu_oracle_rate(w, filt, n_queries):
             codes, scales = codecs.e4m3_leaf_quantise(vals)
             vals = codecs.e4m3_leaf_dequantise(codes, scales)
         ref = textures.Sparse3D(w["origins"][sub], vals)
+    elif w["name"] == "neural":
+        from oracle import mlp, neural
+        h16 = lambda a: codecs.f16_decode(codecs.f16_encode(np.asarray(a, dtype=np.float64)))
+        P = mlp.unflatten(np.asarray(w["trained_params"], dtype=np.float64))
+        for k in ("W1", "W2", "W3"):
+            P[k] = h16(P[k])
+        lat, o, levels = w["trained_latents"], 0, []
+        for L in range(w["nlat"]):
+            m = max(1, w["size"] >> L)
+            levels.append(h16(lat[o:o + m * m]).reshape(m, m, 8))
+            o += m * m
+        ref = neural.NeuralTexture2D(levels, P, [h16(p) for p in w["pyramid"][w["nlat"]:]])
     else:
         ref = textures.Texture2D([w["values"].astype(np.float64)])
     q = w["coords"][:n_queries]
@@ -260,7 +303,10 @@ def cpu_oracle_rate(w, filt, n_queries):
     for a in range(0, q.shape[0], 1 << 20):
         b = min(q.shape[0], a + (1 << 20))
         qid = np.arange(a, b, dtype=np.uint64)
-        if w["name"] != "tex2d":
+        if w["name"] == "neural":
+            filters.lookup_2d(ref, q[a:b], w["lod"][a:b], filt, stochastic_form=True, seed=1, qid=qid,
+                              level_mode=filters.LEVEL_NEAREST)
+        elif w["name"] != "tex2d":
             filters.lookup_3d(ref, q[a:b], filt, stochastic_form=True, seed=1, qid=qid)
         else:
             filters.lookup_2d(ref, q[a:b], None, filt, stochastic_form=True, seed=1, qid=qid)
@@ -275,7 +321,9 @@ def run_reference(args):
     if rank != 0:
         return 0
     w = make_workload(args.workload)
-    n_sample = 1 << 20 if args.workload.startswith("sparse") else 1 << 21
+    if args.workload == "neural":
+        w["trained_params"], w["trained_latents"] = w["params"], w["latents"]
+    n_sample = 1 << 20 if args.workload.startswith("sparse") or args.workload == "neural" else 1 << 21
     rates = []
     for k in range(args.warmup + args.steps):
         r, _ = cpu_oracle_rate(w, args.filter, n_sample)
@@ -316,21 +364,29 @@ def run_ours(args):
     stf.load()
 
     w = make_workload(args.workload)
-    tex = make_texture(stf, w)
+    tex = make_texture(stf, w, train_steps=args.train_steps)
     n = w["coords"].shape[0]
     C = w["channels"]
     coords = torch.from_numpy(w["coords"]).to(dev)
     out = torch.empty((n, C), dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
     filt = args.filter
+    lod = torch.from_numpy(w["lod"]).to(dev) if "lod" in w else None
+    # the neural workload compares one decode with the 4-decode bilinear filter at one level
+    level_mode = stf.LEVEL_NEAREST if w["name"] == "neural" else stf.LEVEL_STOCHASTIC
+
+    # weak scaling: every rank filters its own full batch; rank r's queries are the
+    # r-th block of one world-wide batch (query_offset = r * n), so no two ranks
+    # share variates and nothing is exchanged
+    qoff = rank * n
 
     def stochastic(f=filt, **kw):
-        p = stf.make_params(f, seed=2024, **kw)
-        return lambda: stf.stf_lookup_batch(tex.handle, p, coords, None, n, out, None, stream)
+        p = stf.make_params(f, seed=2024, level_mode=level_mode, query_offset=qoff, **kw)
+        return lambda: stf.stf_lookup_batch(tex.handle, p, coords, lod, n, out, None, stream)
 
     def deterministic(f):
-        p = stf.make_params(f)
-        return lambda: stf.stf_lookup_batch_deterministic(tex.handle, p, coords, None, n, out, stream)
+        p = stf.make_params(f, level_mode=level_mode)
+        return lambda: stf.stf_lookup_batch_deterministic(tex.handle, p, coords, lod, n, out, stream)
 
     with ClockSampler(torch.cuda.current_device()) as clk:
         per, total, win = time_steps(torch, stochastic(), args.steps, args.warmup, stream, dist,
@@ -355,13 +411,16 @@ def run_ours(args):
         # the same queries in a seeded random order (incoherent rays): where binning pays
         g = torch.Generator(device=dev)
         g.manual_seed(7)
-        shuffled = coords[torch.randperm(n, device=dev, generator=g)].contiguous()
-        pshuf = stf.make_params(filt, seed=2024)
-        pshuf_b = stf.make_params(filt, seed=2024, bin_queries=True)
+        order = torch.randperm(n, device=dev, generator=g)
+        shuffled = coords[order].contiguous()
+        lod_shuf = None if lod is None else lod[order].contiguous()
+        pshuf = stf.make_params(filt, seed=2024, level_mode=level_mode, query_offset=qoff)
+        pshuf_b = stf.make_params(filt, seed=2024, level_mode=level_mode, query_offset=qoff,
+                                  bin_queries=True)
         variants += [("stochastic_shuffled", lambda: stf.stf_lookup_batch(
-                          tex.handle, pshuf, shuffled, None, n, out, None, stream)),
+                          tex.handle, pshuf, shuffled, lod_shuf, n, out, None, stream)),
                      ("stochastic_shuffled_binned", lambda: stf.stf_lookup_batch(
-                          tex.handle, pshuf_b, shuffled, None, n, out, None, stream))]
+                          tex.handle, pshuf_b, shuffled, lod_shuf, n, out, None, stream))]
         for name, fn in variants:
             try:
                 p2, t2 = time_steps(torch, fn, max(3, args.steps // 2), 2, stream)
@@ -375,13 +434,17 @@ def run_ours(args):
 
     # end to end: pinned host coords -> device, lookup, device -> host each step
     h_coords = torch.from_numpy(w["coords"]).pin_memory()
+    h_lod = None if lod is None else torch.from_numpy(w["lod"]).pin_memory()
     h_out = torch.empty((n, C), dtype=torch.float32).pin_memory()
     d_in = torch.empty_like(coords)
-    pe = stf.make_params(filt, seed=2024)
+    d_lod = None if lod is None else torch.empty_like(lod)
+    pe = stf.make_params(filt, seed=2024, level_mode=level_mode, query_offset=qoff)
 
     def e2e_step():
         d_in.copy_(h_coords, non_blocking=True)
-        stf.stf_lookup_batch(tex.handle, pe, d_in, None, n, out, None, stream)
+        if d_lod is not None:
+            d_lod.copy_(h_lod, non_blocking=True)
+        stf.stf_lookup_batch(tex.handle, pe, d_in, d_lod, n, out, None, stream)
         h_out.copy_(out, non_blocking=True)
 
     pe2, te2 = time_steps(torch, e2e_step, max(3, args.steps // 2), 2, stream, dist)
@@ -417,14 +480,26 @@ def run_ours(args):
                      "frac": achieved / hbm, "traffic": traffic,
                      "algorithmic_bytes_per_lookup": algo, "peak_source": peak_kind},
         "e2e": {"value": e2e_value, "unit": "lookups/s",
-                "h2d_bytes_per_step": int(w["coords"].nbytes),
+                "h2d_bytes_per_step": int(w["coords"].nbytes + (w["lod"].nbytes if lod is not None else 0)),
                 "d2h_bytes_per_step": int(n * C * 4)},
         "gpu_launches": args.steps,
         "clocks": clk.summary(),
         "extras": extras,
     }
+    if w["name"] == "neural":
+        flops = 2 * (8 * 64 + 64 * 64 + 64 * 7)
+        tflops = flops * n / (avg_launch_ms / 1000.0) / 1e12
+        line["roofline_tensor"] = {"bound": "tensor", "achieved": tflops, "peak": bf16_peak(),
+                                   "unit": "TFLOP/s", "frac": tflops / bf16_peak(),
+                                   "flops_per_lookup": flops, "path": "mma.sync fp16, fp32 accumulate"}
+        line["config"]["train"] = {"steps": args.train_steps, "batch": 1 << 16,
+                                   "loss_first_last": w.get("train_loss")}
+        line["config"]["level_mode"] = "nearest (one decode vs four)"
     if not args.no_cpu_baseline:
-        ns = (1 << 21) if w["name"].startswith("sparse") else (1 << 23)
+        if w["name"] == "neural":
+            p_, z_ = tex.read()
+            w["trained_params"], w["trained_latents"] = p_.cpu().numpy(), z_.cpu().numpy()
+        ns = (1 << 21) if w["name"].startswith("sparse") or w["name"] == "neural" else (1 << 23)
         rate, dt = cpu_oracle_rate(w, filt, ns)
         line["cpu_baseline"] = {"value": rate, "unit": "lookups/s", "cores": 1, "kind": "oracle",
                                 "sample": "first %d queries of the workload, stochastic %s, "
@@ -438,6 +513,8 @@ def run_ours(args):
 
 def main():
     args = parse()
+    if args.filter is None:
+        args.filter = "linear" if args.workload == "neural" else "bspline3"
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

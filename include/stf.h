@@ -60,7 +60,8 @@ typedef enum {
 typedef enum {
   STF_KIND_TEX2D = 0,    /* 2D texture, optional MIP pyramid */
   STF_KIND_DENSE3D = 1,  /* dense voxel grid */
-  STF_KIND_SPARSE3D = 2  /* sparse grid: root -> upper (32^3) -> lower (16^3) -> 8^3 leaves */
+  STF_KIND_SPARSE3D = 2, /* sparse grid: root -> upper (32^3) -> lower (16^3) -> 8^3 leaves */
+  STF_KIND_NEURAL2D = 3  /* neural 2D texture (stf_create_neural_texture) */
 } stf_kind;
 
 typedef enum {
@@ -162,6 +163,72 @@ stf_status stf_lookup_accumulate(stf_texture tex, const stf_lookup_params* param
                                  const float* d_coords, const float* d_lod, int64_t n,
                                  int32_t n_samples, double* d_sum, double* d_sumsq,
                                  void* stream);
+
+/* ---------------------------------------------------------------- neural textures
+ *
+ * A neural texture stores, for MIP levels 0 .. latent_levels-1, one latent texel
+ * of STF_NEURAL_LATENT channels per texel, and a small decoder MLP that maps a
+ * latent texel to the STF_NEURAL_OUT channels of the texel it stands for:
+ *     H1 = relu(z W1 + b1), H2 = relu(H1 W2 + b2), y = H2 W3 + b3
+ * with W1: 8x64, W2: 64x64, W3: 64x7 (row-major [in][out]).  Levels from
+ * latent_levels up to levels-1 hold stored texels (the fallback).  The paper
+ * motivates stochastic filtering for such expensive decoders (Section 1,
+ * Section 5.2): the stochastic lookup decodes the one latent texel it picks, the
+ * deterministic lookup decodes every tap and filters the decoded values.  Latents
+ * and weights are used in binary16 by the tensor-core kernels (float32 masters are
+ * kept for training); biases and accumulation are float32.
+ * stf_lookup_batch / stf_lookup_batch_deterministic take (u, v) coordinates and an
+ * optional level of detail as for 2D textures and write n x 7 floats. */
+#define STF_NEURAL_LATENT 8
+#define STF_NEURAL_HIDDEN 64
+#define STF_NEURAL_OUT 7
+#define STF_NEURAL_PARAMS (8 * 64 + 64 + 64 * 64 + 64 + 64 * 7 + 7) /* 5191 */
+
+typedef struct {
+  int32_t width, height;       /* level-0 size, powers of two */
+  int32_t latent_levels;       /* 1 .. 4 */
+  int32_t levels;              /* total levels >= latent_levels (<= log2(max(w,h)) + 1) */
+  int32_t data_on_device;      /* pointers below are device (1) or host (0) memory */
+  int32_t reserved;
+  const float* latents;        /* [level][y][x][8] for the latent levels, concatenated */
+  const float* params;         /* STF_NEURAL_PARAMS floats: W1, b1, W2, b2, W3, b3 */
+  const float* fallback;       /* [level][y][x][7] for levels latent_levels .. levels-1,
+                                  concatenated; NULL when levels == latent_levels */
+} stf_neural_desc;
+
+/* Create a neural texture (copies the data; synchronises `stream`). */
+stf_status stf_create_neural_texture(const stf_neural_desc* desc, void* stream, stf_texture* out);
+
+/* Loss and gradients of one batch, without changing the texture: texels given as
+ * flat indices over the latent levels (level 0 texels first, row-major), targets as
+ * batch x 7 floats.  d_param_grads (STF_NEURAL_PARAMS floats), d_latent_grads
+ * (batch x 8) and d_loss (one float) may each be NULL; all are overwritten.  The
+ * loss is (1 / batch) * sum over rows and channels of (y - target)^2.  batch must be
+ * a multiple of 32. */
+stf_status stf_neural_gradients(stf_texture tex, const int64_t* d_texels, int64_t batch,
+                                const float* d_target_rows, float* d_param_grads,
+                                float* d_latent_grads, float* d_loss, void* stream);
+
+typedef struct {
+  float lr_latent;   /* Adam step size for the latents */
+  float lr_params;   /* Adam step size for the MLP parameters */
+  float beta1, beta2, eps;
+  int32_t batch;     /* texels per step (multiple of 32, at most the latent texel count) */
+  uint64_t seed;     /* keys the permutation that orders texels into batches */
+} stf_train_config;
+
+/* Run `steps` Adam steps on the loss above.  Step s (counted from the texture's
+ * creation) trains on texels perm((s * batch + i) mod N), i < batch, where perm is a
+ * seeded bijection of the N latent texels, so every texel is visited once per epoch
+ * and a batch holds distinct texels.  d_target holds the target texels of the
+ * latent levels, [level][y][x][7] concatenated (float32, device).  d_loss_per_step,
+ * if not NULL, receives one float per step. */
+stf_status stf_neural_train(stf_texture tex, const float* d_target, const stf_train_config* cfg,
+                            int32_t steps, float* d_loss_per_step, void* stream);
+
+/* Copy the current float32 parameters (STF_NEURAL_PARAMS floats) and, if
+ * d_latents is not NULL, the float32 latents ([level][y][x][8]) to device memory. */
+stf_status stf_neural_read(stf_texture tex, float* d_params, float* d_latents, void* stream);
 
 /* Largest n accepted by stf_lookup_batch_binned_noalloc. */
 #define STF_NOALLOC_MAX_QUERIES (1 << 20)

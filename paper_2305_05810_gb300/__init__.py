@@ -17,10 +17,13 @@ __all__ = [
     "stf_texture_bytes", "stf_synchronize", "stf_last_error", "stf_version", "Texture",
     "KIND_TEX2D", "KIND_DENSE3D", "KIND_SPARSE3D", "FMT_F32", "FMT_F16", "FMT_E4M3_SCALED",
     "FILTER_LINEAR", "FILTER_BSPLINE3", "FILTER_CATMULL_ROM", "LEVEL_NEAREST",
-    "LEVEL_STOCHASTIC", "library_path", "load",
+    "LEVEL_STOCHASTIC", "library_path", "load", "NeuralDesc", "TrainConfig",
+    "stf_create_neural_texture", "stf_neural_gradients", "stf_neural_train", "stf_neural_read",
+    "NeuralTexture", "KIND_NEURAL2D",
 ]
 
-KIND_TEX2D, KIND_DENSE3D, KIND_SPARSE3D = 0, 1, 2
+KIND_TEX2D, KIND_DENSE3D, KIND_SPARSE3D, KIND_NEURAL2D = 0, 1, 2, 3
+NEURAL_LATENT, NEURAL_HIDDEN, NEURAL_OUT, NEURAL_PARAMS = 8, 64, 7, 5191
 FMT_F32, FMT_F16, FMT_E4M3_SCALED = 0, 1, 2
 FILTER_LINEAR, FILTER_BSPLINE3, FILTER_CATMULL_ROM = 0, 1, 2
 FILTERS = {"linear": FILTER_LINEAR, "bspline3": FILTER_BSPLINE3, "catmull_rom": FILTER_CATMULL_ROM}
@@ -55,6 +58,20 @@ class LookupParams(ctypes.Structure):
                 ("reuse_xi", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
+class NeuralDesc(ctypes.Structure):
+    _fields_ = [("width", ctypes.c_int32), ("height", ctypes.c_int32),
+                ("latent_levels", ctypes.c_int32), ("levels", ctypes.c_int32),
+                ("data_on_device", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("latents", ctypes.c_void_p), ("params", ctypes.c_void_p),
+                ("fallback", ctypes.c_void_p)]
+
+
+class TrainConfig(ctypes.Structure):
+    _fields_ = [("lr_latent", ctypes.c_float), ("lr_params", ctypes.c_float),
+                ("beta1", ctypes.c_float), ("beta2", ctypes.c_float), ("eps", ctypes.c_float),
+                ("batch", ctypes.c_int32), ("seed", ctypes.c_uint64)]
+
+
 _lib = None
 
 
@@ -84,11 +101,16 @@ def load(build_if_missing=True):
     lib.stf_last_error.restype = ctypes.c_char_p
     lib.stf_last_error.argtypes = []
     lib.stf_version.restype = I32
+    lib.stf_create_neural_texture.argtypes = [P(NeuralDesc), VP, P(VP)]
+    lib.stf_neural_gradients.argtypes = [VP, VP, I64, VP, VP, VP, VP, VP]
+    lib.stf_neural_train.argtypes = [VP, VP, P(TrainConfig), I32, VP, VP]
+    lib.stf_neural_read.argtypes = [VP, VP, VP, VP]
     lib.stf_debug_fail_allocation.argtypes = [I64]
     lib.stf_debug_fail_allocation.restype = None
     for f in ("stf_create_texture", "stf_destroy", "stf_lookup_batch",
               "stf_lookup_batch_deterministic", "stf_lookup_accumulate", "stf_texture_bytes",
-              "stf_synchronize", "stf_lookup_batch_binned_noalloc"):
+              "stf_synchronize", "stf_lookup_batch_binned_noalloc", "stf_create_neural_texture",
+              "stf_neural_gradients", "stf_neural_train", "stf_neural_read"):
         getattr(lib, f).restype = I32
     _lib = lib
     return lib
@@ -129,6 +151,28 @@ def stf_create_texture(desc, stream=None):
     h = ctypes.c_void_p()
     _check(load().stf_create_texture(ctypes.byref(desc), _stream(stream), ctypes.byref(h)))
     return h.value
+
+
+def stf_create_neural_texture(desc, stream=None):
+    h = ctypes.c_void_p()
+    _check(load().stf_create_neural_texture(ctypes.byref(desc), _stream(stream), ctypes.byref(h)))
+    return h.value
+
+
+def stf_neural_gradients(tex, texels, batch, target_rows, param_grads=None, latent_grads=None,
+                         loss=None, stream=None):
+    _check(load().stf_neural_gradients(tex, _ptr(texels), int(batch), _ptr(target_rows),
+                                       _ptr(param_grads), _ptr(latent_grads), _ptr(loss),
+                                       _stream(stream)))
+
+
+def stf_neural_train(tex, target, config, steps, loss_per_step=None, stream=None):
+    _check(load().stf_neural_train(tex, _ptr(target), ctypes.byref(config), int(steps),
+                                   _ptr(loss_per_step), _stream(stream)))
+
+
+def stf_neural_read(tex, params=None, latents=None, stream=None):
+    _check(load().stf_neural_read(tex, _ptr(params), _ptr(latents), _stream(stream)))
 
 
 def stf_destroy(tex):
@@ -236,3 +280,46 @@ class Texture:
         stf_lookup_accumulate(self.handle, make_params(**params), coords, lod, n, n_samples, s, s2,
                               stream)
         return s, s2
+
+
+class NeuralTexture(Texture):
+    """Owning wrapper around a neural texture (latent levels + decoder MLP)."""
+
+    def __init__(self, width, height, latent_levels, levels, latents, params, fallback=None,
+                 stream=None):
+        import torch
+        dev = torch.device("cuda", torch.cuda.current_device())
+        f32 = lambda a: (a if isinstance(a, torch.Tensor) else torch.as_tensor(a)).to(dev, torch.float32).contiguous()
+        lat, par = f32(latents), f32(params)
+        fb = None if fallback is None else f32(fallback)
+        desc = NeuralDesc(width=width, height=height, latent_levels=latent_levels, levels=levels,
+                          data_on_device=1, latents=lat.data_ptr(), params=par.data_ptr(),
+                          fallback=None if fb is None else fb.data_ptr())
+        self.kind, self.channels = KIND_NEURAL2D, NEURAL_OUT
+        self.n_latent_texels = lat.numel() // NEURAL_LATENT
+        self.handle = stf_create_neural_texture(desc, stream)
+
+    def gradients(self, texels, targets, stream=None):
+        import torch
+        n = texels.shape[0]
+        pg = torch.empty(NEURAL_PARAMS, dtype=torch.float32, device=texels.device)
+        lg = torch.empty((n, NEURAL_LATENT), dtype=torch.float32, device=texels.device)
+        loss = torch.empty(1, dtype=torch.float32, device=texels.device)
+        stf_neural_gradients(self.handle, texels, n, targets, pg, lg, loss, stream)
+        return pg, lg, loss
+
+    def train(self, target, steps, batch=65536, lr_latent=1e-2, lr_params=1e-3, seed=0, stream=None):
+        import torch
+        cfg = TrainConfig(lr_latent=lr_latent, lr_params=lr_params, beta1=0.9, beta2=0.999,
+                          eps=1e-8, batch=batch, seed=seed)
+        losses = torch.empty(max(1, steps), dtype=torch.float32, device=target.device)
+        stf_neural_train(self.handle, target, cfg, steps, losses, stream)
+        return losses[:steps]
+
+    def read(self, stream=None):
+        import torch
+        dev = torch.device("cuda", torch.cuda.current_device())
+        p = torch.empty(NEURAL_PARAMS, dtype=torch.float32, device=dev)
+        z = torch.empty((self.n_latent_texels, NEURAL_LATENT), dtype=torch.float32, device=dev)
+        stf_neural_read(self.handle, p, z, stream)
+        return p, z

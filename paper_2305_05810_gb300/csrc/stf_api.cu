@@ -75,6 +75,7 @@ static void free_texture(stf_texture_s* t) {
   if (!t) return;
   cudaFree(t->d_texels);
   cudaFree(t->d_tree);
+  cudaFree(t->d_neural);
   cudaFree(t->d_status);
   cudaFree(t->d_scratch);
   t->magic = 0;
@@ -125,6 +126,26 @@ static stf_status create_grid(stf_texture_s* t, const stf_texture_desc* d, cudaS
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   cudaFree(tmp);
   return e == cudaSuccess ? STF_OK : fail_cuda(e, "texture build");
+}
+
+// Status word, registration; frees the texture if creation failed.
+static stf_status finish_create(stf_texture_s* t, stf_status st, stf_texture* out) {
+  if (st == STF_OK) {
+    cudaError_t e = dev_alloc((void**)&t->d_status, sizeof(unsigned));
+    if (e == cudaSuccess) e = cudaMemset(t->d_status, 0, sizeof(unsigned));
+    if (e != cudaSuccess) st = fail_cuda(e, "status word");
+    t->sparse.status = t->d_status;
+  }
+  if (st != STF_OK) {
+    free_texture(t);
+    return st;
+  }
+  {
+    std::lock_guard<std::mutex> lk(g_registry_mutex);
+    g_registry.insert(t);
+  }
+  *out = t;
+  return STF_OK;
 }
 
 extern "C" {
@@ -199,22 +220,19 @@ stf_status stf_create_texture(const stf_texture_desc* d, void* stream, stf_textu
     default:
       st = fail(STF_ERR_INVALID_ARGUMENT, "unknown texture kind %d", d->kind);
   }
-  if (st == STF_OK) {
-    cudaError_t e = dev_alloc((void**)&t->d_status, sizeof(unsigned));
-    if (e == cudaSuccess) e = cudaMemset(t->d_status, 0, sizeof(unsigned));
-    if (e != cudaSuccess) st = fail_cuda(e, "status word");
-    t->sparse.status = t->d_status;
-  }
-  if (st != STF_OK) {
-    free_texture(t);
-    return st;
-  }
-  {
-    std::lock_guard<std::mutex> lk(g_registry_mutex);
-    g_registry.insert(t);
-  }
-  *out = t;
-  return STF_OK;
+  return finish_create(t, st, out);
+}
+
+stf_status stf_create_neural_texture(const stf_neural_desc* d, void* stream, stf_texture* out) {
+  if (!out) return fail(STF_ERR_INVALID_ARGUMENT, "out handle pointer is NULL");
+  *out = nullptr;
+  if (!d) return fail(STF_ERR_INVALID_ARGUMENT, "descriptor is NULL");
+  stf_texture_s* t = new stf_texture_s();
+  memset(t, 0, sizeof(*t));
+  t->magic = STF_TEX_MAGIC;
+  t->kind = STF_KIND_NEURAL2D;
+  t->format = STF_FMT_F16;
+  return finish_create(t, build_neural(t, d, (cudaStream_t)stream), out);
 }
 
 stf_status stf_destroy(stf_texture t) {
@@ -266,11 +284,12 @@ stf_status check_lookup(stf_texture t, const stf_lookup_params* p, const float* 
     return fail(STF_ERR_INVALID_ARGUMENT, "unknown level mode %d", p->level_mode);
   if (n == 0) return STF_OK;
   if (!coords || !out) return fail(STF_ERR_INVALID_ARGUMENT, "coords or out is NULL");
-  if (lod && t->kind != STF_KIND_TEX2D)
+  const bool is2d = t->kind == STF_KIND_TEX2D || t->kind == STF_KIND_NEURAL2D;
+  if (lod && !is2d)
     return fail(STF_ERR_UNSUPPORTED, "level of detail is only meaningful for 2D textures");
-  const size_t ca = t->kind == STF_KIND_TEX2D ? 8 : 4;
+  const size_t ca = is2d ? 8 : 4;
   if ((uintptr_t)coords % ca) return fail(STF_ERR_INVALID_ARGUMENT, "coords not %zu-byte aligned", ca);
-  const size_t oa = t->channels >= 4 ? 16 : (size_t)t->channels * 4;
+  const size_t oa = t->kind == STF_KIND_NEURAL2D ? 4 : (t->channels >= 4 ? 16 : (size_t)t->channels * 4);
   if ((uintptr_t)out % oa) return fail(STF_ERR_INVALID_ARGUMENT, "out not %zu-byte aligned", oa);
   return STF_OK;
 }
@@ -322,6 +341,10 @@ stf_status dispatch(Op op, stf_texture t, int filter, const LookupArgs& a, cudaS
     case STF_KIND_TEX2D: e = launch_tex2d(op, filter, t->format, t->channels, view2d(t), a, s); break;
     case STF_KIND_DENSE3D: e = launch_dense3d(op, filter, t->format, view3d(t), a, s); break;
     case STF_KIND_SPARSE3D: e = launch_sparse3d(op, filter, t->format, t->sparse, a, s); break;
+    case STF_KIND_NEURAL2D:
+      if (op == OP_ACCUMULATE) return fail(STF_ERR_UNSUPPORTED, "accumulation is not offered for neural textures");
+      e = launch_neural(op, filter, t->neural, a, s);
+      break;
   }
   return e == cudaSuccess ? STF_OK : fail_cuda(e, "lookup launch");
 }

@@ -209,12 +209,12 @@ static cudaError_t pool_alloc(void** p, size_t bytes, cudaStream_t s) {
 
 BinSpec bin_spec(const stf_texture_s* t) {
   BinSpec b;
-  b.dims = t->kind == STF_KIND_TEX2D ? 2 : 3;
+  b.dims = (t->kind == STF_KIND_TEX2D || t->kind == STF_KIND_NEURAL2D) ? 2 : 3;
   b.scale_x = (float)t->dims[0];
   b.scale_y = (float)t->dims[1];
   if (t->kind == STF_KIND_SPARSE3D) {
     b.shift = 8;
-  } else if (t->kind == STF_KIND_TEX2D) {
+  } else if (b.dims == 2) {
     const int ext = t->dims[0] > t->dims[1] ? t->dims[0] : t->dims[1];
     int sh = 2;
     while ((ext >> sh) > 32) ++sh;

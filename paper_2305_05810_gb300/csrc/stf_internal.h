@@ -19,6 +19,10 @@ LookupArgs make_args(const stf_lookup_params* p, const float* coords, const floa
 // Sparse grid construction (stf_sparse.cu).
 stf_status build_sparse(stf_texture_s* t, const stf_texture_desc* d, cudaStream_t s);
 
+// Neural textures (stf_neural.cu).
+stf_status build_neural(stf_texture_s* t, const stf_neural_desc* d, cudaStream_t s);
+cudaError_t launch_neural(Op op, int filter, const NeuralDev& nd, const LookupArgs& a, cudaStream_t s);
+
 // Morton-binned stochastic lookup (stf_binning.cu).
 stf_status lookup_binned(stf_texture t, int filter, const LookupArgs& a, cudaStream_t s);
 

@@ -1,5 +1,6 @@
 // Internal types shared by the library's translation units (not part of the ABI).
 #pragma once
+#include <cuda_fp16.h>
 #include <stdint.h>
 
 #include "../../include/stf.h"
@@ -33,6 +34,22 @@ struct SparseDev {
   unsigned* status;
 };
 
+// Device view of a neural texture (stf_neural.cu).
+struct NeuralDev {
+  const __half* lat16;        // [texel][8], latent levels
+  float* lat32;               // float32 master latents (training)
+  float* m_lat;
+  float* v_lat;
+  const __half* fb16;         // [texel][8] (7 + pad), fallback levels
+  const __half* wimg;         // weight images
+  const float* bias;          // nn::NBIAS floats
+  int64_t lvl_off[STF_MAX_LEVELS];   // texel offset within lat16 (latent) or fb16 (fallback)
+  int32_t lvl_w[STF_MAX_LEVELS];
+  int32_t lvl_h[STF_MAX_LEVELS];
+  int32_t nlat, nlev;
+  int64_t n_lat_texels;
+};
+
 }  // namespace stf
 
 struct stf_texture_s {
@@ -48,6 +65,15 @@ struct stf_texture_s {
   // sparse tree (one allocation, views into it)
   void* d_tree;
   stf::SparseDev sparse;
+  // neural texture: one allocation holding latents, optimizer state and weights
+  void* d_neural;
+  stf::NeuralDev neural;
+  float* n_params;    // float32 parameters
+  float* n_m;         // Adam moments of the parameters
+  float* n_v;
+  float* n_grads;
+  float* n_loss;      // one float
+  int64_t n_step;     // training steps taken
   // device status word
   unsigned* d_status;
   // binning scratch, grown on demand

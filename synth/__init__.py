@@ -157,3 +157,31 @@ C2_RAYS = dict(W=1920, H=1080, steps=16, centre=(128.0, 128.0, 128.0), radius=38
                half_span=222.0, seed=3)
 C3_RAYS = dict(W=2048, H=2048, steps=16, centre=(1024.0, 1024.0, 1024.0), radius=3072.0,
                half_span=1774.0, seed=4)
+
+
+def box_levels(level0, num_levels):
+    """Box-filtered pyramid of a power-of-two image (H, W, C): level L texel = mean of
+    the level-0 block it covers.  Returns a list of float32 arrays."""
+    base = np.asarray(level0, dtype=np.float64)
+    H, W, C = base.shape
+    out = [np.asarray(level0, dtype=np.float32)]
+    for L in range(1, num_levels):
+        hl, wl = max(1, H >> L), max(1, W >> L)
+        out.append(base.reshape(hl, H // hl, wl, W // wl, C).mean(axis=(1, 3)).astype(np.float32))
+    return out
+
+
+def neural_init(size, latent_levels, seed=5, latent_scale=0.5):
+    """Initial neural-texture state: latents ~ N(0, latent_scale^2) for every texel of
+    the latent levels ([level][y][x][8] concatenated) and He-initialised decoder
+    weights with zero biases, flat (W1 8x64, b1, W2 64x64, b2, W3 64x7, b3)."""
+    rng = np.random.default_rng(seed)
+    n = sum(max(1, size >> L) ** 2 for L in range(latent_levels))
+    latents = (rng.standard_normal((n, 8)) * latent_scale).astype(np.float32)
+    parts = []
+    for fan_in, shape in ((8, (8, 64)), (64, (64,)), (64, (64, 64)), (64, (64,)), (64, (64, 7)), (7, (7,))):
+        if len(shape) == 2:
+            parts.append(rng.standard_normal(shape).reshape(-1) * np.sqrt(2.0 / shape[0]))
+        else:
+            parts.append(np.zeros(shape[0]))
+    return latents, np.concatenate(parts).astype(np.float32)
