@@ -52,7 +52,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="dense",
-                    choices=["dense", "tex2d", "sparse", "sparse_e4m3", "neural"])
+                    choices=["dense", "tex2d", "sparse", "sparse_e4m3", "neural", "serving"])
+    ap.add_argument("--requests", type=int, default=600, help="serving: number of requests")
     ap.add_argument("--train-steps", type=int, default=400)
     ap.add_argument("--filter", default=None, choices=["linear", "bspline3", "catmull_rom"],
                     help="default: bspline3 (linear for the neural workload)")
@@ -222,23 +223,26 @@ def pct(xs, p):
     return xs[i]
 
 
-def kernel_hash():
+KERNEL_SOURCES = {"dense": "stf_grid.cu", "tex2d": "stf_grid.cu", "sparse": "stf_sparse.cu",
+                  "sparse_e4m3": "stf_sparse.cu", "neural": "stf_neural.cu"}
+
+
+def kernel_hash(workload):
+    """Hash of the sources that build the workload's lookup kernel."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2305_05810_gb300", "csrc")
-    for f in sorted(os.listdir(csrc)):
-        if f.endswith((".cu", ".cuh", ".h")):
-            h.update(open(os.path.join(csrc, f), "rb").read())
+    for f in ("stf_device.cuh", "stf_types.h", "stf_launch.h", KERNEL_SOURCES[workload]):
+        h.update(open(os.path.join(csrc, f), "rb").read())
     return h.hexdigest()[:16]
 
 
-def ncu_traffic(key):
-    """DRAM bytes per launch from the committed ncu summary, if it was taken on the
-    current kernel sources; else None."""
+def ncu_traffic(workload, filt):
+    """DRAM bytes per launch of the stochastic kernel from the committed ncu summary,
+    if it was captured on the current kernel sources; else None."""
     p = os.path.join(ROOT, "profiles", "ncu_traffic.json")
     try:
-        d = json.load(open(p))
-        e = d.get(key)
-        if e and e.get("kernel_hash") == kernel_hash():
+        e = json.load(open(p)).get("%s_stochastic_%s" % (workload, filt))
+        if e and e.get("kernel_hash") == kernel_hash(workload):
             return e["dram_bytes_per_launch"]
     except (OSError, ValueError):
         pass
@@ -315,6 +319,69 @@ def cpu_oracle_rate(w, filt, n_queries):
 
 
 # ------------------------------------------------------------------ arms
+
+def run_serving(args):
+    """Continuous-batching serving over the four resident textures (2D, dense,
+    sparse, neural): log-uniform request sizes in [1K, 4M] queries, mixed filters,
+    stochastic/deterministic 50/50, 16 GB admission budget, 8 slots.  Capacity is
+    first measured closed-loop (all requests queued at once); then requests arrive
+    as a Poisson process at 70% of that capacity and latency is arrival -> results
+    on the host."""
+    import torch
+    import paper_2305_05810_gb300 as stf
+    from paper_2305_05810_gb300 import serving
+    stf.load()
+    ws = {k: make_workload(k) for k in ("tex2d", "dense", "sparse", "neural")}
+    textures = {k: make_texture(stf, w, train_steps=args.train_steps) for k, w in ws.items()}
+    pools = {k: torch.from_numpy(w["coords"]).pin_memory() for k, w in ws.items()}
+    lod_pool = torch.from_numpy(ws["neural"]["lod"]).pin_memory()
+    keys = list(textures)
+
+    def make(i, size, rng):
+        key = keys[int(rng.integers(0, len(keys)))]
+        pool = pools[key]
+        start = int(rng.integers(0, pool.shape[0] - size))
+        lod = lod_pool[start:start + size] if key == "neural" else None
+        filt = ("linear", "bspline3", "catmull_rom")[int(rng.integers(0, 3))]
+        lm = stf.LEVEL_NEAREST if key == "neural" else stf.LEVEL_STOCHASTIC
+        return serving.Request(i, key, pool[start:start + size], lod, filter=filt,
+                               stochastic=bool(rng.integers(0, 2)), seed=1000 + i, level_mode=lm)
+
+    def run(rate):
+        reqs = serving.poisson_requests(args.requests, rate, (1000, 4 << 20), make, seed=6)
+        backend = serving.TorchBackend(textures, n_slots=8)
+        sched = serving.Scheduler(backend, n_slots=8, budget_bytes=16 << 30, chunk_queries=1 << 20)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        done = sched.run(reqs, realtime=rate is not None)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        return done, sched, dt
+
+    run(None)                                   # warm-up (allocator, pinned buffers)
+    done, sched, dt = run(None)                 # closed loop: capacity
+    total = sum(r.n for r in done)
+    capacity = total / dt
+    mean_size = total / len(done)
+    rate = 0.7 * capacity / mean_size
+    done, sched, dt = run(rate)
+    total = sum(r.n for r in done)
+    lat = serving.latency_summary(done)
+    line = {"metric": "serving: lookups/s and p50/p99 request latency (mixed textures)",
+            "value": total / dt, "unit": "lookups/s", "n_gpus": 1, "higher_is_better": True,
+            "p50_ms": lat["p50_ms"], "p99_ms": lat["p99_ms"], "mean_ms": lat["mean_ms"],
+            "requests": len(done), "arrival_rate_per_s": rate,
+            "closed_loop_capacity_lookups_per_s": capacity,
+            "peak_admitted": sched.peak_active, "peak_device_bytes": sched.peak_in_use,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "serving over 2D, dense, sparse and neural textures",
+                       "sizes": "log-uniform 1K-4M", "slots": 8, "budget_bytes": 16 << 30,
+                       "chunk_queries": 1 << 20, "stochastic_fraction": 0.5}}
+    print(json.dumps(line), flush=True)
+    for T in textures.values():
+        T.close()
+    return 0
+
 
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
@@ -463,7 +530,7 @@ def run_ours(args):
     algo = ALGO_BYTES[(w["name"], "stochastic")]
     avg_launch_ms = statistics.mean(per)
     achieved = algo * n / (avg_launch_ms / 1000.0) / 1e9
-    traffic = ncu_traffic("%s_stochastic_%s" % (w["name"], filt))
+    traffic = ncu_traffic(w["name"], filt)
     line = {
         "metric": "filtered lookups/s (stochastic, %s)" % filt,
         "value": value, "unit": "lookups/s", "n_gpus": world, "steps": args.steps,
@@ -517,6 +584,8 @@ def main():
         args.filter = "linear" if args.workload == "neural" else "bspline3"
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "serving":
+        return run_serving(args)
     return run_ours(args)
 
 
