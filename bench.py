@@ -348,7 +348,8 @@ def run_serving(args):
                                stochastic=bool(rng.integers(0, 2)), seed=1000 + i, level_mode=lm)
 
     def run(rate):
-        reqs = serving.poisson_requests(args.requests, rate, (1000, 4 << 20), make, seed=6)
+        # closed loop (rate None): the same request sequence, all queued at the start
+        reqs = serving.poisson_requests(args.requests, rate or 1.0, (1000, 4 << 20), make, seed=6)
         backend = serving.TorchBackend(textures, n_slots=8)
         sched = serving.Scheduler(backend, n_slots=8, budget_bytes=16 << 30, chunk_queries=1 << 20)
         torch.cuda.synchronize()

@@ -172,71 +172,131 @@ struct NeuralSmem {
   float y[4][32][8];       // per warp: 32 rows x 8 floats
 };
 
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const uint32_t d = (uint32_t)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(gmem));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
+
+// Per-lane state of one 32-query chunk between tap choice and output.
+struct NeuralPick {
+  int64_t j;      // caller's query slot
+  float sigma;    // estimator scale (Catmull-Rom)
+  int4 tap;
+  int mode;       // 0: no texel (background), 1: decode the latent, 2: stored fallback texel
+};
+
+// Tap choice for query i of the chunk; starts the 16-byte gather of the chosen texel
+// (latent or fallback) into the lane's shared-memory row.
 template <int F>
-__global__ void __launch_bounds__(128) k_neural_stochastic(NeuralDev nd, LookupArgs a) {
-  __shared__ __align__(16) NeuralSmem s;
+__device__ __forceinline__ NeuralPick neural_pick(const NeuralDev& nd, const LookupArgs& a, int64_t i,
+                                                  uint4* row) {
+  NeuralPick pk;
+  pk.j = 0;
+  pk.sigma = 1.0f;
+  pk.tap = make_int4(0, 0, 0, -1);
+  pk.mode = 0;
+  if (i >= a.n) return pk;
+  pk.j = query_slot(a, i);
+  const float2 uv = reinterpret_cast<const float2*>(a.coords)[i];
+  const float lod = a.lod ? a.lod[i] : 0.0f;
+  const uint4 r = query_variates(a, pk.j, a.sample_index);
+  int L = 0;
+  if (a.lod != nullptr && nd.nlev > 1) {
+    const float lc = fminf(fmaxf(lod, 0.0f), (float)(nd.nlev - 1));
+    L = min((int)floorf(__fadd_rn(lc, a.level_mode == STF_LEVEL_NEAREST ? 0.5f : unit24(r.w))), nd.nlev - 1);
+  }
+  const int w = nd.lvl_w[L], h = nd.lvl_h[L];
+  float x[2] = {__fsub_rn(__fmul_rn(uv.x, (float)w), 0.5f), __fsub_rn(__fmul_rn(uv.y, (float)h), 0.5f)};
+  if (!(prepare_coords<2>(x) && isfinite(lod))) return pk;
+  const float u[2] = {unit24(r.x), unit24(r.y)};
+  int idx[2];
+  pk.sigma = pick_taps<F, 2, false>(x, u, idx);
+  pk.tap = make_int4(idx[0], idx[1], 0, L);
+  const int cx = min(max(idx[0], 0), w - 1), cy = min(max(idx[1], 0), h - 1);
+  const __half* base = L < nd.nlat ? nd.lat16 : nd.fb16;
+  cp_async16(row, base + (nd.lvl_off[L] + (int64_t)cy * w + cx) * 8);
+  pk.mode = L < nd.nlat ? 1 : 2;
+  return pk;
+}
+
+struct NeuralStochSmem {
+  uint32_t w[nn::IMG_FWD / 2];
+  float b[nn::NBIAS];
+  uint4 rows[4][2][32];    // per warp, double-buffered texel rows
+  float y[4][32][8];       // per warp: decoded rows, then the final values
+};
+
+// Stochastic lookup: one latent texel decoded per query.  Software-pipelined per
+// warp: the gathers of the next 32-query chunk are in flight (cp.async) while the
+// MLP runs on the current chunk; results are staged in shared memory and written
+// back in coalesced 128-byte rows when the chunk's slots are contiguous.
+template <int F>
+__global__ void __launch_bounds__(128, 4) k_neural_stochastic(NeuralDev nd, LookupArgs a) {
+  __shared__ __align__(16) NeuralStochSmem s;
   stage_weights(nd, s.w, s.b, nn::IMG_FWD / 2);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   uint32_t a2[2][4][4], a3[2][4][4];
   const int64_t nwarps = (int64_t)gridDim.x * 4;
-  for (int64_t c = (int64_t)blockIdx.x * 4 + warp; c * 32 < a.n; c += nwarps) {
+  int64_t c = (int64_t)blockIdx.x * 4 + warp;
+  if (c * 32 >= a.n) return;
+  int buf = 0;
+  NeuralPick cur = neural_pick<F>(nd, a, c * 32 + lane, &s.rows[warp][0][lane]);
+  cp_async_commit();
+  for (; c * 32 < a.n; c += nwarps) {
+    const int64_t cn = c + nwarps;
+    NeuralPick nxt;
+    if (cn * 32 < a.n) nxt = neural_pick<F>(nd, a, cn * 32 + lane, &s.rows[warp][buf ^ 1][lane]);
+    cp_async_commit();
+    cp_async_wait<1>();      // this chunk's texels have landed
+    __syncwarp();
+    mlp_forward<2>(s.w, s.b, reinterpret_cast<const uint32_t*>(s.rows[warp][buf]), 0, s.y[warp], a2, a3);
+    __syncwarp();
+    float v[8];
+    if (cur.mode == 1) {
+#pragma unroll
+      for (int k = 0; k < 7; ++k) v[k] = s.y[warp][lane][k] * cur.sigma;
+    } else if (cur.mode == 2) {
+      const uint4 t4 = s.rows[warp][buf][lane];
+      const uint32_t* tw = reinterpret_cast<const uint32_t*>(&t4);
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const float2 f = unpack_h2(tw[k]);
+        v[2 * k] = f.x * cur.sigma;
+        v[2 * k + 1] = f.y * cur.sigma;
+      }
+    } else {
+#pragma unroll
+      for (int k = 0; k < 7; ++k) v[k] = 0.0f;
+    }
     const int64_t i = c * 32 + lane;
     const bool live = i < a.n;
-    float out[8];
-    bool fetched = false, decode = false;
-    float sigma = 1.0f;
-    int4 tap = make_int4(0, 0, 0, -1);
-    uint4 texel = make_uint4(0, 0, 0, 0);
-    int64_t j = 0;
-    if (live) {
-      j = query_slot(a, i);
-      const float2 uv = reinterpret_cast<const float2*>(a.coords)[i];
-      const float lod = a.lod ? a.lod[i] : 0.0f;
-      const uint4 r = query_variates(a, j, a.sample_index);
-      int L = 0;
-      if (a.lod != nullptr && nd.nlev > 1) {
-        const float lc = fminf(fmaxf(lod, 0.0f), (float)(nd.nlev - 1));
-        L = min((int)floorf(__fadd_rn(lc, a.level_mode == STF_LEVEL_NEAREST ? 0.5f : unit24(r.w))),
-                nd.nlev - 1);
+    if (a.perm == nullptr) {
+      // contiguous slots: stage the 32 x 7 floats and write them as coalesced rows
+      __syncwarp();
+#pragma unroll
+      for (int k = 0; k < 7; ++k) s.y[warp][0][lane * 7 + k] = v[k];
+      __syncwarp();
+      const int64_t nrows = min((int64_t)32, a.n - c * 32);
+      float* dst = a.out + c * 32 * 7;
+      const float* src = &s.y[warp][0][0];
+#pragma unroll
+      for (int k = 0; k < 7; ++k) {
+        const int e = lane + 32 * k;
+        if (e < nrows * 7) dst[e] = src[e];
       }
-      float x[2] = {__fsub_rn(__fmul_rn(uv.x, (float)nd.lvl_w[L]), 0.5f),
-                    __fsub_rn(__fmul_rn(uv.y, (float)nd.lvl_h[L]), 0.5f)};
-      if (prepare_coords<2>(x) && isfinite(lod)) {
-        const float u[2] = {unit24(r.x), unit24(r.y)};
-        int idx[2];
-        sigma = pick_taps<F, 2, false>(x, u, idx);
-        tap = make_int4(idx[0], idx[1], 0, L);
-        texel = neural_texel(nd, L, idx[0], idx[1]);
-        fetched = true;
-        decode = L < nd.nlat;
-      }
+    } else if (live) {
+#pragma unroll
+      for (int k = 0; k < 7; ++k) a.out[cur.j * 7 + k] = v[k];
     }
-    reinterpret_cast<uint4*>(s.a[warp])[lane] = decode ? texel : make_uint4(0, 0, 0, 0);
+    if (live && a.taps) reinterpret_cast<int4*>(a.taps)[cur.j] = cur.tap;
     __syncwarp();
-    mlp_forward<2>(s.w, s.b, s.a[warp], 0, s.y[warp], a2, a3);
-    __syncwarp();
-    if (live) {
-      if (decode) {
-#pragma unroll
-        for (int k = 0; k < 7; ++k) out[k] = s.y[warp][lane][k] * sigma;
-      } else if (fetched) {
-        const uint32_t* tw = reinterpret_cast<const uint32_t*>(&texel);
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-          const float2 f = unpack_h2(tw[k]);
-          out[2 * k] = f.x * sigma;
-          out[2 * k + 1] = f.y * sigma;
-        }
-      } else {
-#pragma unroll
-        for (int k = 0; k < 7; ++k) out[k] = 0.0f;
-      }
-#pragma unroll
-      for (int k = 0; k < 7; ++k) a.out[j * 7 + k] = out[k];
-      if (a.taps) reinterpret_cast<int4*>(a.taps)[j] = tap;
-    }
-    __syncwarp();
+    cur = nxt;
+    buf ^= 1;
   }
+  cp_async_wait<0>();
 }
 
 // Deterministic: every tap of the filter window (at one level, or two blended by
