@@ -135,6 +135,7 @@ static stf_status finish_create(stf_texture_s* t, stf_status st, stf_texture* ou
     if (e == cudaSuccess) e = cudaMemset(t->d_status, 0, sizeof(unsigned));
     if (e != cudaSuccess) st = fail_cuda(e, "status word");
     t->sparse.status = t->d_status;
+    t->neural.status = t->d_status;
   }
   if (st != STF_OK) {
     free_texture(t);

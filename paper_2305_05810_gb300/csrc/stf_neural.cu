@@ -222,81 +222,280 @@ __device__ __forceinline__ NeuralPick neural_pick(const NeuralDev& nd, const Loo
   return pk;
 }
 
-struct NeuralStochSmem {
-  uint32_t w[nn::IMG_FWD / 2];
-  float b[nn::NBIAS];
-  uint4 rows[4][2][32];    // per warp, double-buffered texel rows
-  float y[4][32][8];       // per warp: decoded rows, then the final values
+// ---------------------------------------------------------------- tcgen05 decode
+//
+// The stochastic decode on the fifth-generation tensor cores: for a tile of 128
+// queries (one per thread) the chosen latent texels are gathered into a shared-memory
+// A tile; one elected thread issues the three layers as tcgen05.mma (M = 128, binary16
+// operands from shared memory, float32 accumulators in tensor memory); after each
+// layer every thread loads its own accumulator row with tcgen05.ld, adds the bias,
+// applies ReLU, rounds to binary16 and writes the next layer's A tile.  Operand tiles
+// use the no-swizzle K-major layout: 8-row x 16-byte core matrices, core matrices
+// along K 128 bytes apart (LBO), 8-row groups K/8 * 128 bytes apart (SBO).
+
+namespace tc {
+
+constexpr int ROWS = 128;            // queries per tile = threads per CTA
+constexpr int TMEM_COLS = 128;       // D1/D2 in columns 0..63, D3 in 64..79
+constexpr int A1_BYTES = ROWS * 16 * 2, A2_BYTES = ROWS * 64 * 2;
+constexpr int B1_BYTES = 64 * 16 * 2, B2_BYTES = 64 * 64 * 2, B3_BYTES = 16 * 64 * 2;
+
+// byte offset of element (r, k) in an R x K tile (K = 16 or 64)
+__host__ __device__ constexpr int off(int r, int k, int K) {
+  return (r >> 3) * (K / 8) * 128 + (k >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2;
+}
+
+__device__ __forceinline__ uint64_t desc(const void* p, int K) {
+  const uint32_t a = (uint32_t)__cvta_generic_to_shared(p);
+  uint64_t d = (uint64_t)((a & 0x3FFFF) >> 4);
+  d |= (uint64_t)(128 >> 4) << 16;                 // LBO: next core matrix along K
+  d |= (uint64_t)(((K / 8) * 128) >> 4) << 32;     // SBO: next 8-row group
+  d |= (uint64_t)1 << 46;                           // descriptor version; no swizzle
+  return d;
+}
+
+// kind::f16 instruction descriptor: F32 accumulate, F16 A and B, both K-major.
+__host__ __device__ constexpr uint32_t idesc(int M, int N) {
+  return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t id, uint32_t acc) {
+  asm volatile(
+      "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+      "l"(a), "l"(b), "r"(id), "r"(acc));
+}
+
+__device__ __forceinline__ void commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+      (uint32_t)__cvta_generic_to_shared(bar)));
+}
+
+// Wait for phase `parity` of the mbarrier, at most ~2^22 polls; false on timeout.
+__device__ __forceinline__ bool wait_bar(uint64_t* bar, uint32_t parity) {
+  const uint32_t a = (uint32_t)__cvta_generic_to_shared(bar);
+  uint32_t done = 0;
+  for (int it = 0; it < (1 << 22) && !done; ++it) {
+    asm volatile(
+        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done) : "r"(a), "r"(parity));
+  }
+  return done != 0;
+}
+
+template <int N>
+__device__ __forceinline__ void tmem_ld(uint32_t taddr, uint32_t* r);
+
+template <>
+__device__ __forceinline__ void tmem_ld<32>(uint32_t taddr, uint32_t* r) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;");
+}
+
+template <>
+__device__ __forceinline__ void tmem_ld<8>(uint32_t taddr, uint32_t* r) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+               : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;");
+}
+
+struct Smem {
+  unsigned char b1[B1_BYTES];
+  unsigned char b2[B2_BYTES];
+  unsigned char b3[B3_BYTES];
+  unsigned char a1[2][A1_BYTES];
+  unsigned char a2[A2_BYTES];
+  float bias[nn::NBIAS];
+  float out[ROWS * 7];
+  uint64_t bar;
+  uint32_t tmem;
+  int abort;
 };
 
-// Stochastic lookup: one latent texel decoded per query.  Software-pipelined per
-// warp: the gathers of the next 32-query chunk are in flight (cp.async) while the
-// MLP runs on the current chunk; results are staged in shared memory and written
-// back in coalesced 128-byte rows when the chunk's slots are contiguous.
-template <int F>
-__global__ void __launch_bounds__(128, 4) k_neural_stochastic(NeuralDev nd, LookupArgs a) {
-  __shared__ __align__(16) NeuralStochSmem s;
-  stage_weights(nd, s.w, s.b, nn::IMG_FWD / 2);
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  uint32_t a2[2][4][4], a3[2][4][4];
-  const int64_t nwarps = (int64_t)gridDim.x * 4;
-  int64_t c = (int64_t)blockIdx.x * 4 + warp;
-  if (c * 32 >= a.n) return;
-  int buf = 0;
-  NeuralPick cur = neural_pick<F>(nd, a, c * 32 + lane, &s.rows[warp][0][lane]);
-  cp_async_commit();
-  for (; c * 32 < a.n; c += nwarps) {
-    const int64_t cn = c + nwarps;
-    NeuralPick nxt;
-    if (cn * 32 < a.n) nxt = neural_pick<F>(nd, a, cn * 32 + lane, &s.rows[warp][buf ^ 1][lane]);
-    cp_async_commit();
-    cp_async_wait<1>();      // this chunk's texels have landed
-    __syncwarp();
-    mlp_forward<2>(s.w, s.b, reinterpret_cast<const uint32_t*>(s.rows[warp][buf]), 0, s.y[warp], a2, a3);
-    __syncwarp();
-    float v[8];
-    if (cur.mode == 1) {
+}  // namespace tc
+
+// Hidden layer epilogue: D (64 float32 per row, tensor memory) + bias -> ReLU ->
+// binary16 row of the next A tile.
+__device__ __forceinline__ void tc_hidden(uint32_t taddr, const float* bias, unsigned char* a2, int row) {
 #pragma unroll
-      for (int k = 0; k < 7; ++k) v[k] = s.y[warp][lane][k] * cur.sigma;
-    } else if (cur.mode == 2) {
-      const uint4 t4 = s.rows[warp][buf][lane];
+  for (int half = 0; half < 2; ++half) {
+    uint32_t r[32];
+    tc::tmem_ld<32>(taddr + 32 * half, r);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      uint32_t w[4];
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const int c = 8 * q + 2 * e;
+        const float lo = __uint_as_float(r[c]) + bias[32 * half + c];
+        const float hi = __uint_as_float(r[c + 1]) + bias[32 * half + c + 1];
+        // ReLU and round to binary16 in one instruction (the first source goes to the
+        // upper half)
+        asm("cvt.rn.relu.f16x2.f32 %0, %1, %2;" : "=r"(w[e]) : "f"(hi), "f"(lo));
+      }
+      *reinterpret_cast<uint4*>(a2 + tc::off(row, 32 * half + 8 * q, 64)) = make_uint4(w[0], w[1], w[2], w[3]);
+    }
+  }
+}
+
+template <int F>
+__global__ void __launch_bounds__(128) k_neural_stochastic_tc(NeuralDev nd, LookupArgs a) {
+  extern __shared__ __align__(1024) unsigned char dyn[];
+  tc::Smem& s = *reinterpret_cast<tc::Smem*>(dyn);
+  const int tid = threadIdx.x, warp = tid >> 5;
+  // weights: binary16 images -> K-major no-swizzle B tiles (16-byte rows)
+  {
+    const uint4* img = reinterpret_cast<const uint4*>(nd.wimg);
+    for (int e = tid; e < 64 * 2; e += 128) {        // W1^T: n < 64, k chunks of 8 (< 16)
+      const int n = e >> 1, kc = e & 1;
+      *reinterpret_cast<uint4*>(s.b1 + tc::off(n, 8 * kc, 16)) = __ldg(img + (nn::I_W1T + n * 24 + 8 * kc) / 8);
+    }
+    for (int e = tid; e < 64 * 8; e += 128) {        // W2^T: n < 64, k chunks of 8 (< 64)
+      const int n = e >> 3, kc = e & 7;
+      *reinterpret_cast<uint4*>(s.b2 + tc::off(n, 8 * kc, 64)) = __ldg(img + (nn::I_W2T + n * 72 + 8 * kc) / 8);
+    }
+    for (int e = tid; e < 16 * 8; e += 128) {        // W3^T: n < 16 (rows >= 8 zero)
+      const int n = e >> 3, kc = e & 7;
+      *reinterpret_cast<uint4*>(s.b3 + tc::off(n, 8 * kc, 64)) =
+          n < 8 ? __ldg(img + (nn::I_W3T + n * 72 + 8 * kc) / 8) : make_uint4(0, 0, 0, 0);
+    }
+    for (int k = tid; k < nn::NBIAS; k += 128) s.bias[k] = __ldg(nd.bias + k);
+    for (int b = 0; b < 2; ++b)                      // latent columns 8..15 of A1 stay zero
+      *reinterpret_cast<uint4*>(s.a1[b] + tc::off(tid, 8, 16)) = make_uint4(0, 0, 0, 0);
+  }
+  if (tid == 0) {
+    s.abort = 0;
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"((uint32_t)__cvta_generic_to_shared(&s.bar)));
+    asm volatile("fence.mbarrier_init.release.cluster;");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     (uint32_t)__cvta_generic_to_shared(&s.tmem)), "n"(tc::TMEM_COLS));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  const uint32_t tmem = s.tmem;
+  const uint32_t trow = tmem + ((uint32_t)(32 * warp) << 16);   // this warp's 32 lanes
+  uint32_t parity = 0;
+  const int64_t ntiles = (a.n + tc::ROWS - 1) / tc::ROWS;
+  int64_t tile = blockIdx.x;
+  int buf = 0;
+  NeuralPick cur;
+  if (tile < ntiles)
+    cur = neural_pick<F>(nd, a, tile * tc::ROWS + tid, reinterpret_cast<uint4*>(s.a1[0] + tc::off(tid, 0, 16)));
+  cp_async_commit();
+  for (; tile < ntiles; tile += gridDim.x) {
+    const int64_t next = tile + gridDim.x;
+    NeuralPick nxt;
+    if (next < ntiles)
+      nxt = neural_pick<F>(nd, a, next * tc::ROWS + tid,
+                           reinterpret_cast<uint4*>(s.a1[buf ^ 1] + tc::off(tid, 0, 16)));
+    cp_async_commit();
+    cp_async_wait<1>();
+    asm volatile("fence.proxy.async.shared::cta;");
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    if (s.abort) break;
+    // layer 1: D[0, 64) = A1 (128 x 16) * W1 (16 x 64)
+    // one thread issues and waits; the others park in the barrier without issuing
+    if (tid == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;");
+      tc::mma(tmem, tc::desc(s.a1[buf], 16), tc::desc(s.b1, 16), tc::idesc(128, 64), 0);
+      tc::commit(&s.bar);
+      if (!tc::wait_bar(&s.bar, parity)) s.abort = 1;
+    }
+    parity ^= 1;
+    __syncthreads();
+    if (s.abort) break;
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    tc_hidden(trow, s.bias, s.a2, tid);
+    asm volatile("fence.proxy.async.shared::cta;");
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    // layer 2: D[0, 64) = H1 (128 x 64) * W2 (64 x 64)
+    if (tid == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;");
+#pragma unroll
+      for (int kk = 0; kk < 4; ++kk)
+        tc::mma(tmem, tc::desc(s.a2 + kk * 256, 64), tc::desc(s.b2 + kk * 256, 64), tc::idesc(128, 64), kk);
+      tc::commit(&s.bar);
+      if (!tc::wait_bar(&s.bar, parity)) s.abort = 1;
+    }
+    parity ^= 1;
+    __syncthreads();
+    if (s.abort) break;
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    tc_hidden(trow, s.bias + 64, s.a2, tid);
+    asm volatile("fence.proxy.async.shared::cta;");
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    // layer 3: D[64, 80) = H2 (128 x 64) * W3 (64 x 16)
+    if (tid == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;");
+#pragma unroll
+      for (int kk = 0; kk < 4; ++kk)
+        tc::mma(tmem + 64, tc::desc(s.a2 + kk * 256, 64), tc::desc(s.b3 + kk * 256, 64), tc::idesc(128, 16), kk);
+      tc::commit(&s.bar);
+      if (!tc::wait_bar(&s.bar, parity)) s.abort = 1;
+    }
+    parity ^= 1;
+    __syncthreads();
+    if (s.abort) break;
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    float v[8];
+    {
+      uint32_t r[8];
+      tc::tmem_ld<8>(trow + 64, r);
+#pragma unroll
+      for (int k = 0; k < 7; ++k) v[k] = __uint_as_float(r[k]) + s.bias[128 + k];
+    }
+    if (cur.mode == 2) {          // stored fallback texel, fetched into the A1 row
+      const uint4 t4 = *reinterpret_cast<const uint4*>(s.a1[buf] + tc::off(tid, 0, 16));
       const uint32_t* tw = reinterpret_cast<const uint32_t*>(&t4);
 #pragma unroll
       for (int k = 0; k < 4; ++k) {
         const float2 f = unpack_h2(tw[k]);
-        v[2 * k] = f.x * cur.sigma;
-        v[2 * k + 1] = f.y * cur.sigma;
+        v[2 * k] = f.x;
+        v[2 * k + 1] = f.y;
       }
-    } else {
+    } else if (cur.mode == 0) {
 #pragma unroll
       for (int k = 0; k < 7; ++k) v[k] = 0.0f;
     }
-    const int64_t i = c * 32 + lane;
+#pragma unroll
+    for (int k = 0; k < 7; ++k) v[k] *= cur.sigma;
+    const int64_t i = tile * tc::ROWS + tid;
     const bool live = i < a.n;
     if (a.perm == nullptr) {
-      // contiguous slots: stage the 32 x 7 floats and write them as coalesced rows
-      __syncwarp();
 #pragma unroll
-      for (int k = 0; k < 7; ++k) s.y[warp][0][lane * 7 + k] = v[k];
-      __syncwarp();
-      const int64_t nrows = min((int64_t)32, a.n - c * 32);
-      float* dst = a.out + c * 32 * 7;
-      const float* src = &s.y[warp][0][0];
-#pragma unroll
-      for (int k = 0; k < 7; ++k) {
-        const int e = lane + 32 * k;
-        if (e < nrows * 7) dst[e] = src[e];
-      }
+      for (int k = 0; k < 7; ++k) s.out[tid * 7 + k] = v[k];
+      __syncthreads();
+      const int64_t nrows = min((int64_t)tc::ROWS, a.n - tile * tc::ROWS);
+      float* dst = a.out + tile * tc::ROWS * 7;
+      for (int e = tid; e < nrows * 7; e += 128) dst[e] = s.out[e];
     } else if (live) {
 #pragma unroll
       for (int k = 0; k < 7; ++k) a.out[cur.j * 7 + k] = v[k];
     }
     if (live && a.taps) reinterpret_cast<int4*>(a.taps)[cur.j] = cur.tap;
-    __syncwarp();
     cur = nxt;
     buf ^= 1;
   }
   cp_async_wait<0>();
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  if (s.abort && tid == 0) atomicOr(nd.status, STF_DEV_MMA_TIMEOUT);
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "n"(tc::TMEM_COLS));
 }
 
 // Deterministic: every tap of the filter window (at one level, or two blended by
@@ -793,7 +992,23 @@ __global__ void k_rows_to_h8(const float* src, int cin, __half* dst, int64_t row
 template <int F>
 static cudaError_t run_neural(Op op, const NeuralDev& nd, const LookupArgs& a, cudaStream_t s) {
   const int blocks = grid_blocks(a.n, 128);
-  if (op == OP_STOCHASTIC) k_neural_stochastic<F><<<blocks, 128, 0, s>>>(nd, a);
+  if (op == OP_STOCHASTIC) {
+    // 56 KiB of shared memory per CTA keeps at most 4 CTAs on an SM, so their
+    // 4 x 128 tensor-memory columns fit in the SM's 512
+    const int smem = (int)sizeof(tc::Smem) + 1024 > 56 * 1024 ? (int)sizeof(tc::Smem) + 1024 : 56 * 1024;
+    static bool attr = false;
+    if (!attr) {
+      cudaFuncSetAttribute(k_neural_stochastic_tc<F>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+      attr = true;
+    }
+    int sms = 0, dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int64_t tiles = (a.n + tc::ROWS - 1) / tc::ROWS;
+    const int grid = (int)(tiles < (int64_t)sms * 4 ? tiles : (int64_t)sms * 4);
+    k_neural_stochastic_tc<F><<<grid, 128, smem, s>>>(nd, a);
+    return cudaGetLastError();
+  }
   else if (op == OP_DETERMINISTIC) k_neural_deterministic<F><<<blocks, 128, 0, s>>>(nd, a);
   else return cudaErrorNotSupported;
   return cudaGetLastError();

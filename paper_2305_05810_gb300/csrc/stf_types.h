@@ -10,6 +10,7 @@
 
 // Device status word bits (set by kernels with atomicOr, read by stf_synchronize).
 #define STF_DEV_BAD_NODE 1u        // sparse traversal met an index outside its arrays
+#define STF_DEV_MMA_TIMEOUT 2u     // a tensor-core completion wait gave up
 
 namespace stf {
 
@@ -48,6 +49,7 @@ struct NeuralDev {
   int32_t lvl_h[STF_MAX_LEVELS];
   int32_t nlat, nlev;
   int64_t n_lat_texels;
+  unsigned* status;           // device status word
 };
 
 }  // namespace stf

@@ -158,26 +158,48 @@ class Scheduler:
 
 
 class TorchBackend:
-    """Device side of the scheduler: torch streams, pinned host buffers, the C ABI."""
+    """Device side of the scheduler: torch streams, pinned host buffers, the C ABI.
 
-    def __init__(self, textures, n_slots=8, device=None):
+    Each slot owns device buffers (coordinates, levels of detail, results) and a
+    pinned host buffer for results; all grow to the largest request the slot has
+    served and are then reused, so admitting a request allocates nothing (device and
+    pinned-host allocations synchronise and would stall the other slots).  With
+    keep_results the result of each request is copied out of the slot's pinned buffer
+    into its own host tensor; otherwise ``on_result(request, view)`` (if given) sees
+    the pinned view before the slot is reused."""
+
+    def __init__(self, textures, n_slots=8, device=None, keep_results=True, on_result=None):
         import torch
         self.torch = torch
         self.textures = textures                       # key -> stf.Texture
         self.device = device or torch.device("cuda", torch.cuda.current_device())
         self.streams = [torch.cuda.Stream(device=self.device) for _ in range(n_slots)]
+        self.slot_bufs = [{} for _ in range(n_slots)]
+        self.keep_results = keep_results
+        self.on_result = on_result
 
     def channels(self, key):
         return self.textures[key].channels
 
+    def _buf(self, slot, name, numel, host=False):
+        b = self.slot_bufs[slot].get(name)
+        if b is None or b.numel() < numel:
+            if host:
+                b = self.torch.empty(max(numel, 1 << 16), dtype=self.torch.float32, pin_memory=True)
+            else:
+                with self.torch.cuda.stream(self.streams[slot]):
+                    b = self.torch.empty(max(numel, 1 << 16), dtype=self.torch.float32, device=self.device)
+            self.slot_bufs[slot][name] = b
+        return b
+
     def begin(self, req, slot):
         torch = self.torch
         T = self.textures[req.texture]
-        with torch.cuda.stream(self.streams[slot]):
-            d_coords = torch.empty(tuple(req.coords.shape), dtype=torch.float32, device=self.device)
-            d_lod = None if req.lod is None else torch.empty((req.n,), dtype=torch.float32, device=self.device)
-            d_out = torch.empty((req.n, T.channels), dtype=torch.float32, device=self.device)
-        h_out = torch.empty((req.n, T.channels), dtype=torch.float32, pin_memory=True)
+        d = req.coords.shape[1]
+        d_coords = self._buf(slot, "coords", req.n * d)[: req.n * d].view(req.n, d)
+        d_lod = None if req.lod is None else self._buf(slot, "lod", req.n)[: req.n]
+        d_out = self._buf(slot, "out", req.n * T.channels)[: req.n * T.channels].view(req.n, T.channels)
+        h_out = self._buf(slot, "h_out", req.n * T.channels, host=True)[: req.n * T.channels].view(req.n, T.channels)
         params = stf.make_params(req.filter, seed=req.seed, level_mode=req.level_mode)
         return {"T": T, "d_coords": d_coords, "d_lod": d_lod, "d_out": d_out, "h_out": h_out,
                 "params": params}
@@ -208,7 +230,9 @@ class TorchBackend:
         return ev.query()
 
     def finish(self, st, req):
-        return st["h_out"]
+        if self.on_result is not None:
+            self.on_result(req, st["h_out"])
+        return st["h_out"].clone() if self.keep_results else None
 
 
 def poisson_requests(n, rate_per_s, sizes, make, seed=6):
