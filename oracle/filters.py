@@ -166,6 +166,115 @@ def expectation_by_enumeration(fetch, xs32, filt, power=1):
     return total
 
 
+# ---------------------------------------------------------------- positivization
+
+def _block_masses(weights, dims):
+    """Per-axis inner (taps 1, 2) and outer (taps 0, 3) |w| sums, and the masses of the
+    2^D blocks (bit a of the block set = axis a takes an outer tap)."""
+    ain = [np.abs(w[1]) + np.abs(w[2]) for w in weights]
+    aout = [np.abs(w[0]) + np.abs(w[3]) for w in weights]
+    masses = []
+    for b in range(1 << dims):
+        m = np.ones_like(ain[0])
+        for a in range(dims):
+            m = m * (aout[a] if (b >> a) & 1 else ain[a])
+        masses.append(m)
+    return masses
+
+
+def _blocks_of_sign(dims, sign):
+    """Blocks whose taps carry that sign: (-1)^(number of outer axes)."""
+    return [b for b in range(1 << dims) if (-1) ** bin(b).count("1") == sign]
+
+
+def positivized(fetch, xs32, u_pos, u_neg, background=0.0):
+    """Two-tap positivized estimate of the Catmull-Rom filter (Section 2.2,
+    "Positivization"; Appendix B): <F> = W+ t(j+) - W- t(j-), where W+ and W- are the
+    sums of the positive and of the absolute negative weights and j+ / j- are drawn
+    from each set with probability proportional to |w|.
+
+    Reading for separable cubic weights with signs (-, +, +, -) on each axis: the
+    2^D blocks "inner (taps 1, 2) or outer (taps 0, 3) on each axis" partition the
+    taps by sign (an even number of outer axes is positive).  A set is sampled by
+    choosing one of its blocks with probability proportional to its mass (variate
+    u[D]), then on each axis a tap of the block's pair with probability proportional
+    to |w| (variate u[a]).  Decisions in float32 as for `stochastic`; the negative
+    sample is skipped when W- is zero.  u_pos / u_neg: lists of D + 1 variates.
+    Returns (value, positive tap indices, negative tap indices, exempt, finite)."""
+    D = len(xs32)
+    N = np.asarray(xs32[0]).shape[0]
+    frames = [axis_frame(x) for x in xs32]
+    finite = np.logical_and.reduce([fin for (_, _, fin) in frames])
+    w64 = [axis_weights(f, "catmull_rom") for (_, f, _) in frames]
+    w32 = [np.abs(w).astype(np.float32) for w in w64]
+    m64 = _block_masses(w64, D)
+    m32 = _block_masses([w for w in w32], D)     # float32 arithmetic throughout
+    exempt = np.zeros(N, dtype=bool)
+    out = {}
+    with np.errstate(invalid="ignore", divide="ignore"):   # empty sets (W = 0) are unused
+        for sign, u in ((1, u_pos), (-1, u_neg)):
+            out[sign] = _sample_set(D, sign, u, w64, m64, m32, frames, exempt)
+    Wp, ip = out[1]
+    Wn, ineg = out[-1]
+    val = Wp[:, None] * fetch(*ip)
+    neg = Wn > 0
+    if np.any(neg):
+        tn = fetch(*ineg)
+        val = val - np.where(neg, Wn, 0.0)[:, None] * tn
+    val[~finite] = background
+    return val, ip, ineg, exempt & finite, finite
+
+
+def _sample_set(D, sign, u, w64, m64, m32, frames, exempt):
+    """One sign's block and per-axis taps (see `positivized`); updates exempt."""
+    blocks = _blocks_of_sign(D, sign)
+    W = np.sum([m64[b] for b in blocks], axis=0)
+    # block choice: inverse CDF over the set's blocks in increasing order
+    C = np.cumsum(np.stack([m32[b] for b in blocks]).astype(np.float32), axis=0, dtype=np.float32)
+    us = (np.asarray(u[D], dtype=np.float32) * C[-1]).astype(np.float32)
+    kb = np.sum(us[None, :] >= C[:-1], axis=0)
+    chosen = np.asarray(blocks)[kb]
+    Wb = np.stack([m64[b] for b in blocks])
+    interior = np.cumsum(Wb, axis=0)[:-1] / np.where(W > 0, W, 1)
+    exempt |= (W > 0) & (np.min(np.abs(np.asarray(u[D])[None, :] - interior), axis=0) < EXEMPT)
+    idx = []
+    for a in range(D):
+        outer = (chosen >> a) & 1
+        pair = np.where(outer[None, :] == 1, w64[a][[0, 3]], w64[a][[1, 2]])
+        k, _ = select_tap(u[a], pair)
+        exempt |= (W > 0) & (boundary_distance(u[a], pair) < EXEMPT)
+        tap = np.where(outer == 1, np.where(k == 0, 0, 3), np.where(k == 0, 1, 2))
+        idx.append(frames[a][0] - 1 + tap)
+    return W, idx
+
+
+def positivized_expectation(fetch, xs32):
+    """Exact expectation of `positivized` by enumerating both sets' blocks and taps:
+    sum over positive (block, taps) of p * W+ t  minus  the same over negative ones."""
+    D = len(xs32)
+    frames = [axis_frame(x) for x in xs32]
+    w64 = [axis_weights(f, "catmull_rom") for (_, f, _) in frames]
+    m64 = _block_masses(w64, D)
+    total = 0.0
+    for sign in (1, -1):
+        blocks = _blocks_of_sign(D, sign)
+        W = np.sum([m64[b] for b in blocks], axis=0)
+        for b in blocks:
+            pb = np.where(W > 0, m64[b] / np.where(W > 0, W, 1), 0.0)
+            pairs = [((0, 3) if (b >> a) & 1 else (1, 2)) for a in range(D)]
+            for combo in itertools.product((0, 1), repeat=D):
+                p = pb.copy()
+                idx = []
+                for a in range(D):
+                    t0, t1 = pairs[a]
+                    tap = (t0, t1)[combo[a]]
+                    s = np.abs(w64[a][t0]) + np.abs(w64[a][t1])
+                    p = p * np.where(s > 0, np.abs(w64[a][tap]) / np.where(s > 0, s, 1), 0.0)
+                    idx.append(frames[a][0] - 1 + tap)
+                total = total + (sign * p * W)[:, None] * fetch(*idx)
+    return total
+
+
 # ---------------------------------------------------------------- texture wrappers
 
 def _level_choice(lod32, nlev, level_mode, u_level, stochastic_form):
@@ -215,6 +324,18 @@ def lookup_2d(tex, uv, lod, filt, *, stochastic_form, level_mode=LEVEL_STOCHASTI
     L0, L1, a, exempt = _level_choice(lod_in, nlev if lod32 is not None else 1,
                                       level_mode, u[3], stochastic_form)
     taps = np.zeros((N, 4), dtype=np.int64)
+    if stochastic_form and filt == "catmull_rom_positivized":
+        x, y = _raster(uv32, tex, L0)
+        u1 = query_variates(qid, sample_index, seed, stream=1)
+        val, idx, _, ex, fin = positivized(lambda ix, iy: tex.fetch(L0, ix, iy), [x, y],
+                                           [u[0], u[1], u[2]], [u1[0], u1[1], u1[2]])
+        fin &= ~bad_lod
+        val[~fin] = 0.0
+        taps[:, 0], taps[:, 1], taps[:, 3] = idx[0], idx[1], L0
+        taps[~fin] = (0, 0, 0, -1)
+        return val, taps, (exempt | ex) & fin
+    if filt == "catmull_rom_positivized":
+        filt = "catmull_rom"          # the deterministic twin is the Catmull-Rom filter
     if stochastic_form:
         x, y = _raster(uv32, tex, L0)
         val, idx, ex, fin = stochastic(lambda ix, iy: tex.fetch(L0, ix, iy), [x, y], filt,
@@ -239,6 +360,19 @@ def lookup_3d(grid, p, filt, *, stochastic_form, qid=None, sample_index=0, seed=
     p32 = np.asarray(p, dtype=np.float32).reshape(-1, 3)
     N = p32.shape[0]
     xs = [p32[:, 0], p32[:, 1], p32[:, 2]]
+    if filt == "catmull_rom_positivized":
+        if not stochastic_form:
+            return deterministic(grid.fetch, xs, "catmull_rom", grid.background), None, None
+        if qid is None:
+            qid = np.arange(N, dtype=np.uint64)
+        u0 = query_variates(qid, sample_index, seed, stream=0)
+        u1 = query_variates(qid, sample_index, seed, stream=1)
+        val, idx, _, ex, fin = positivized(grid.fetch, xs, [u0[0], u0[1], u0[2], u0[3]],
+                                           [u1[0], u1[1], u1[2], u1[3]], grid.background)
+        taps = np.zeros((N, 4), dtype=np.int64)
+        taps[:, 0], taps[:, 1], taps[:, 2] = idx
+        taps[~fin] = (0, 0, 0, -1)
+        return val, taps, ex & fin
     if not stochastic_form:
         return deterministic(grid.fetch, xs, filt, grid.background), None, None
     if qid is None:

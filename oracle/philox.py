@@ -79,11 +79,12 @@ def philox4x64(ctr, key):
     return philox4(tuple(int(x) for x in ctr), tuple(int(x) for x in key), PHILOX4X64)
 
 
-def query_variates(qid, sample_index, seed):
+def query_variates(qid, sample_index, seed, stream=0):
     """The four uniform variates of one lookup, shape (4, N), float64.
 
-    Counter = (qid low word, qid high word, sample index, 0); key = (seed low
-    word, seed high word).  Each 32-bit output keeps its top 24 bits:
+    Counter = (qid low word, qid high word, sample index, stream); key = (seed low
+    word, seed high word).  Stream 0 serves every filter; the positivized filter also
+    draws stream 1.  Each 32-bit output keeps its top 24 bits:
     u = (r >> 8) * 2^-24, which is exact in both float32 and float64 and lies in
     [0, 1).  Word 0 drives the x axis, 1 the y axis, 2 the z axis and 3 the MIP
     level choice.
@@ -91,6 +92,6 @@ def query_variates(qid, sample_index, seed):
     q = np.asarray(qid, dtype=np.uint64)
     seed = int(seed) & ((1 << 64) - 1)
     r = philox4x32(q & np.uint64(0xFFFFFFFF), q >> np.uint64(32),
-                   np.uint64(int(sample_index) & 0xFFFFFFFF), np.uint64(0),
+                   np.uint64(int(sample_index) & 0xFFFFFFFF), np.uint64(int(stream) & 0xFFFFFFFF),
                    seed & 0xFFFFFFFF, seed >> 32)
     return np.stack([(w >> np.uint64(8)).astype(np.float64) * 2.0 ** -24 for w in r])

@@ -416,3 +416,97 @@ def test_e4m3_leaf_quantisation_error_bound():
     rel = np.abs(deq - leaves) / leaves
     big = leaves >= scales[:, None] * 2.0 ** -6          # normal E4M3 range
     assert np.max(rel[big]) <= 2.0 ** -4 * (1 + 1e-6)
+
+
+# ------------------------------------------------------------------ positivization
+
+def _set_moments(fetch, xs32, sign):
+    """W, E[t] and E[t^2] of one sign's set under the positivized sampler (exact,
+    by enumeration of its blocks and taps)."""
+    D = len(xs32)
+    frames = [filters.axis_frame(x) for x in xs32]
+    w64 = [filters.axis_weights(f, "catmull_rom") for (_, f, _) in frames]
+    m = filters._block_masses(w64, D)
+    blocks = filters._blocks_of_sign(D, sign)
+    W = np.sum([m[b] for b in blocks], axis=0)
+    e1 = e2 = 0.0
+    for b in blocks:
+        pb = np.where(W > 0, m[b] / np.where(W > 0, W, 1), 0)
+        for combo in itertools.product((0, 1), repeat=D):
+            p, idx = pb.copy(), []
+            for a in range(D):
+                t0, t1 = ((0, 3) if (b >> a) & 1 else (1, 2))
+                tap = (t0, t1)[combo[a]]
+                s = np.abs(w64[a][t0]) + np.abs(w64[a][t1])
+                p = p * np.where(s > 0, np.abs(w64[a][tap]) / np.where(s > 0, s, 1), 0)
+                idx.append(frames[a][0] - 1 + tap)
+            t = fetch(*idx)[:, 0]
+            e1 = e1 + p * t
+            e2 = e2 + p * t * t
+    return W, e1, e2
+
+
+@pytest.mark.parametrize("dims", [2, 3])
+def test_positivized_expectation_equals_deterministic(dims):
+    if dims == 2:
+        tex = _tex2d(9, 11, 2, seed=8)
+        fetch = lambda ix, iy: tex.fetch(0, ix, iy)
+        xs = [rng.uniform(-2, 13, 300).astype(np.float32), rng.uniform(-2, 11, 300).astype(np.float32)]
+    else:
+        g = textures.Dense3D(rng.uniform(0, 1, (5, 6, 7)))
+        fetch = g.fetch
+        xs = [rng.uniform(-2, 8, 200).astype(np.float32) for _ in range(3)]
+    e = filters.positivized_expectation(fetch, xs)
+    d = filters.deterministic(fetch, xs, "catmull_rom")
+    assert np.max(np.abs(e - d)) < 1e-12
+
+
+def test_positivized_block_and_tap_frequencies():
+    """The block of each set is drawn with probability mass / W, the tap within it with
+    probability |w| / pair sum (u-lattice frequencies)."""
+    n = 1 << 16
+    u = np.arange(n) / n
+    f = np.float32(0.3)
+    x = np.full(n, 3 + f, dtype=np.float32)
+    y = np.full(n, 5 + np.float32(0.8), dtype=np.float32)
+    tex = textures.Texture2D([np.arange(100.0).reshape(10, 10, 1)])
+    fetch = lambda ix, iy: tex.fetch(0, ix, iy)
+    const = np.full(n, 0.5)
+    _, ip, ineg, _, _ = filters.positivized(fetch, [x, y], [const, const, u], [const, const, u])
+    w = [filters.axis_weights(np.array([0.3]), "catmull_rom")[:, 0],
+         filters.axis_weights(np.array([np.float64(np.float32(0.8))]), "catmull_rom")[:, 0]]
+    ain = [abs(v[1]) + abs(v[2]) for v in w]
+    aout = [abs(v[0]) + abs(v[3]) for v in w]
+    m = {0: ain[0] * ain[1], 1: aout[0] * ain[1], 2: ain[0] * aout[1], 3: aout[0] * aout[1]}
+    outer_x = np.isin(ip[0] - 3, [-1, 2])
+    outer_y = np.isin(ip[1] - 5, [-1, 2])
+    assert abs(np.mean(~outer_x & ~outer_y) - m[0] / (m[0] + m[3])) < 2.0 / n + 1e-6
+    outer_x = np.isin(ineg[0] - 3, [-1, 2])
+    assert abs(np.mean(outer_x) - m[1] / (m[1] + m[2])) < 2.0 / n + 1e-6
+    # within a block, each axis picks its tap by |w| (variate u[a])
+    _, ip, _, _, _ = filters.positivized(fetch, [x, y], [u, const, np.zeros(n)], [const, const, u])
+    assert abs(np.mean(ip[0] == 3) - abs(w[0][1]) / ain[0]) < 2.0 / n + 1e-6
+
+
+def test_positivized_has_lower_variance_than_single_tap():
+    """Positivization (two taps) against the one-tap |w| estimator on a random
+    texture: exact variances, averaged over positions (Section 2.2)."""
+    tex = _tex2d(16, 16, 1, seed=11)
+    fetch = lambda ix, iy: tex.fetch(0, ix, iy)
+    xs = [rng.uniform(2, 13, 400).astype(np.float32), rng.uniform(2, 13, 400).astype(np.float32)]
+    F = filters.deterministic(fetch, xs, "catmull_rom")[:, 0]
+    Wp, p1, p2 = _set_moments(fetch, xs, 1)
+    Wn, n1, n2 = _set_moments(fetch, xs, -1)
+    var_pos = Wp ** 2 * (p2 - p1 ** 2) + Wn ** 2 * (n2 - n1 ** 2)
+    assert np.allclose(Wp * p1 - Wn * n1, F, atol=1e-12)
+    m2 = filters.expectation_by_enumeration(fetch, xs, "catmull_rom", power=2)[:, 0]
+    var_abs = m2 - F ** 2
+    assert np.mean(var_pos) < 0.8 * np.mean(var_abs), (np.mean(var_pos), np.mean(var_abs))
+
+
+def test_positivized_at_texel_centres_returns_texel():
+    tex = _tex2d(8, 8, 1, seed=7)
+    i = rng.integers(2, 6, (100, 2))
+    uv = ((i + 0.5) / 8).astype(np.float32)
+    v, _, _ = filters.lookup_2d(tex, uv, None, "catmull_rom_positivized", stochastic_form=True, seed=2)
+    assert np.array_equal(v, tex.levels[0][i[:, 1], i[:, 0]])
