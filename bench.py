@@ -474,6 +474,9 @@ def run_ours(args):
     extras = {}
     if not args.quick:
         variants = [("deterministic_" + filt, deterministic(filt))]
+        if w["name"] != "neural":
+            variants += [("stochastic_catmull_rom", stochastic("catmull_rom")),
+                         ("stochastic_catmull_rom_positivized", stochastic("catmull_rom_positivized"))]
         if filt != "linear":
             variants += [("stochastic_linear", stochastic("linear")),
                          ("deterministic_linear", deterministic("linear"))]

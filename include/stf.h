@@ -31,7 +31,8 @@
  *     value outside the grid / outside active leaves.
  *   - Random variates: the i-th query of a call draws its variates from
  *     Philox4x32-10 with key = seed and counter = (q, q >> 32, sample_index, 0),
- *     q = query_offset + i.  Results therefore do not depend on how a batch is
+ *     q = query_offset + i (the positivized filter also uses counter word 3 = 1).
+ *     Results therefore do not depend on how a batch is
  *     split into calls, on launch shape, or on what else runs on the GPU.
  */
 #ifndef STF_H_
@@ -74,7 +75,14 @@ typedef enum {
 typedef enum {
   STF_FILTER_LINEAR = 0,     /* tent kernel K1: bilinear / trilinear (Eq. 7, Eq. 8) */
   STF_FILTER_BSPLINE3 = 1,   /* cubic B-spline K_bs, 4 taps per axis (Eq. 9) */
-  STF_FILTER_CATMULL_ROM = 2 /* cubic K3 with a = -1/2 (Appendix A), 4 taps per axis */
+  STF_FILTER_CATMULL_ROM = 2, /* cubic K3 with a = -1/2 (Appendix A), 4 taps per axis;
+                                 stochastic form: one tap by |w| with scale sign * sum|w| */
+  STF_FILTER_CATMULL_ROM_POSITIVIZED = 3 /* the same filter, stochastic form with
+                                 positivization (Section 2.2; Appendix B): one tap from
+                                 the positive and one from the negative weights,
+                                 W+ t(j+) - W- t(j-); two texel fetches, lower variance.
+                                 The deterministic form equals STF_FILTER_CATMULL_ROM.
+                                 reuse_xi is ignored.  Not offered for neural textures. */
 } stf_filter;
 
 typedef enum {

@@ -25,8 +25,9 @@ __all__ = [
 KIND_TEX2D, KIND_DENSE3D, KIND_SPARSE3D, KIND_NEURAL2D = 0, 1, 2, 3
 NEURAL_LATENT, NEURAL_HIDDEN, NEURAL_OUT, NEURAL_PARAMS = 8, 64, 7, 5191
 FMT_F32, FMT_F16, FMT_E4M3_SCALED = 0, 1, 2
-FILTER_LINEAR, FILTER_BSPLINE3, FILTER_CATMULL_ROM = 0, 1, 2
-FILTERS = {"linear": FILTER_LINEAR, "bspline3": FILTER_BSPLINE3, "catmull_rom": FILTER_CATMULL_ROM}
+FILTER_LINEAR, FILTER_BSPLINE3, FILTER_CATMULL_ROM, FILTER_CATMULL_ROM_POSITIVIZED = 0, 1, 2, 3
+FILTERS = {"linear": FILTER_LINEAR, "bspline3": FILTER_BSPLINE3, "catmull_rom": FILTER_CATMULL_ROM,
+           "catmull_rom_positivized": FILTER_CATMULL_ROM_POSITIVIZED}
 LEVEL_NEAREST, LEVEL_STOCHASTIC = 0, 1
 STF_NOALLOC_MAX_QUERIES = 1 << 20   # include/stf.h
 

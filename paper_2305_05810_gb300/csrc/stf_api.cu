@@ -279,8 +279,10 @@ stf_status check_lookup(stf_texture t, const stf_lookup_params* p, const float* 
   if (!handle_ok(t)) return fail(STF_ERR_INVALID_HANDLE, "unknown texture handle");
   if (!p) return fail(STF_ERR_INVALID_ARGUMENT, "params is NULL");
   if (n < 0) return fail(STF_ERR_INVALID_ARGUMENT, "n < 0");
-  if (p->filter < STF_FILTER_LINEAR || p->filter > STF_FILTER_CATMULL_ROM)
+  if (p->filter < STF_FILTER_LINEAR || p->filter > STF_FILTER_CATMULL_ROM_POSITIVIZED)
     return fail(STF_ERR_INVALID_ARGUMENT, "unknown filter %d", p->filter);
+  if (p->filter == STF_FILTER_CATMULL_ROM_POSITIVIZED && t->kind == STF_KIND_NEURAL2D)
+    return fail(STF_ERR_UNSUPPORTED, "positivized filtering is not offered for neural textures");
   if (p->level_mode != STF_LEVEL_NEAREST && p->level_mode != STF_LEVEL_STOCHASTIC)
     return fail(STF_ERR_INVALID_ARGUMENT, "unknown level mode %d", p->level_mode);
   if (n == 0) return STF_OK;

@@ -76,6 +76,9 @@ template <> struct Filter<STF_FILTER_CATMULL_ROM> {
   }
 };
 
+// Positivized Catmull-Rom: the same weights, a different stochastic estimator.
+template <> struct Filter<STF_FILTER_CATMULL_ROM_POSITIVIZED> : Filter<STF_FILTER_CATMULL_ROM> {};
+
 // ---------------------------------------------------------------- tap choice
 // Inverse CDF over |w| (sampling arrays, Section 2.2): tap k is the smallest k with
 // u*S < C_k, C_k = running float32 sum of |w_j|, S = C_{T-1}.  Because u <= 1 - 2^-24
@@ -207,10 +210,75 @@ __device__ __forceinline__ int64_t query_slot(const LookupArgs& a, int64_t i) {
   return a.perm ? (int64_t)__ldg(a.perm + i) : i;
 }
 
-// Philox variates of the caller's query j for one sample index.
-__device__ __forceinline__ uint4 query_variates(const LookupArgs& a, int64_t j, uint32_t sample) {
+// Philox variates of the caller's query j for one sample index (and stream).
+__device__ __forceinline__ uint4 query_variates(const LookupArgs& a, int64_t j, uint32_t sample,
+                                                uint32_t stream = 0u) {
   const uint64_t q = a.query_offset + (uint64_t)j;
-  return philox4x32_10(make_uint4((uint32_t)q, (uint32_t)(q >> 32), sample, 0u), a.key0, a.key1);
+  return philox4x32_10(make_uint4((uint32_t)q, (uint32_t)(q >> 32), sample, stream), a.key0, a.key1);
+}
+
+// Positivization (Section 2.2): with the Catmull-Rom signs (-, +, +, -) on every
+// axis, the 2^D blocks "inner taps (1, 2) or outer taps (0, 3) on each axis"
+// partition the taps by sign (an even number of outer axes is positive).  Each set
+// is sampled once: a block with probability proportional to its mass (variate
+// u[D]; blocks in increasing order, float32 running sums), then on each axis one tap
+// of the block's pair with probability proportional to |w| (variate u[a]).  Returns
+// the positive and negative tap coordinates and W+, W- (sums of |w| in each set).
+template <int D>
+__device__ __forceinline__ void pick_positivized(const float* x, const float* up, const float* un,
+                                                 int* ip, int* in, float& Wp, float& Wn) {
+  using Fl = Filter<STF_FILTER_CATMULL_ROM>;
+  float aw[D][4], ain[D], aout[D];
+  int base[D];
+#pragma unroll
+  for (int a = 0; a < D; ++a) {
+    float f, w[4];
+    base[a] = axis_base(x[a], f) + Fl::OFF0;
+    Fl::weights(f, w);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) aw[a][k] = fabsf(w[k]);
+    ain[a] = __fadd_rn(aw[a][1], aw[a][2]);
+    aout[a] = __fadd_rn(aw[a][0], aw[a][3]);
+  }
+  float m[1 << D];
+#pragma unroll
+  for (int b = 0; b < (1 << D); ++b) {
+    float p = 1.0f;
+#pragma unroll
+    for (int a = 0; a < D; ++a) p = __fmul_rn(p, ((b >> a) & 1) ? aout[a] : ain[a]);
+    m[b] = p;
+  }
+#pragma unroll
+  for (int set = 0; set < 2; ++set) {               // 0: positive (even), 1: negative (odd)
+    const float* u = set ? un : up;
+    float C[(1 << D) / 2];
+    int blk[(1 << D) / 2];
+    float acc = 0.0f;
+    int nb = 0;
+#pragma unroll
+    for (int b = 0; b < (1 << D); ++b)
+      if ((__popc(b) & 1) == set) {
+        acc = __fadd_rn(acc, m[b]);
+        C[nb] = acc;
+        blk[nb] = b;
+        ++nb;
+      }
+    const float us = __fmul_rn(u[D], acc);
+    int chosen = blk[0];
+#pragma unroll
+    for (int j = 0; j < (1 << D) / 2 - 1; ++j)
+      if (us >= C[j]) chosen = blk[j + 1];
+    int* idx = set ? in : ip;
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+      const bool outer = (chosen >> a) & 1;
+      const float w0 = outer ? aw[a][0] : aw[a][1], w1 = outer ? aw[a][3] : aw[a][2];
+      const float s2 = __fadd_rn(w0, w1);
+      const bool second = __fmul_rn(u[a], s2) >= w0;
+      idx[a] = base[a] + (outer ? (second ? 3 : 0) : (second ? 2 : 1));
+    }
+    if (set) Wn = acc; else Wp = acc;
+  }
 }
 
 template <int FMT, int C> struct TexelIO;

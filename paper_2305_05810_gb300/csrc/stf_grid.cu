@@ -38,15 +38,36 @@ __device__ __forceinline__ void tex2d_stochastic_one(const Tex2DView& t, const L
     tap = make_int4(0, 0, 0, -1);
     return;
   }
-  const float u[2] = {unit24(r.x), unit24(r.y)};
-  int idx[2];
-  const float sigma = pick_taps<F, 2, REUSE>(x, u, idx);
-  tap = make_int4(idx[0], idx[1], 0, L);
-  const int cx = min(max(idx[0], 0), W - 1), cy = min(max(idx[1], 0), H - 1);
-  TexelIO<FMT, C>::load(t.texels, t.level_off[L] + (int64_t)cy * W + cx, v);
-  if constexpr (!Filter<F>::NONNEG) {
+  if constexpr (F == STF_FILTER_CATMULL_ROM_POSITIVIZED) {
+    const uint4 r1 = query_variates(a, j, sample, 1u);
+    const float up[3] = {unit24(r.x), unit24(r.y), unit24(r.z)};
+    const float un[3] = {unit24(r1.x), unit24(r1.y), unit24(r1.z)};
+    int ip[2], in[2];
+    float Wp, Wn;
+    pick_positivized<2>(x, up, un, ip, in, Wp, Wn);
+    tap = make_int4(ip[0], ip[1], 0, L);
+    TexelIO<FMT, C>::load(t.texels, t.level_off[L] + (int64_t)min(max(ip[1], 0), H - 1) * W +
+                                        min(max(ip[0], 0), W - 1), v);
 #pragma unroll
-    for (int c = 0; c < C; ++c) v[c] *= sigma;
+    for (int c = 0; c < C; ++c) v[c] *= Wp;
+    if (Wn > 0.0f) {
+      float tn[C];
+      TexelIO<FMT, C>::load(t.texels, t.level_off[L] + (int64_t)min(max(in[1], 0), H - 1) * W +
+                                          min(max(in[0], 0), W - 1), tn);
+#pragma unroll
+      for (int c = 0; c < C; ++c) v[c] = fmaf(-Wn, tn[c], v[c]);
+    }
+  } else {
+    const float u[2] = {unit24(r.x), unit24(r.y)};
+    int idx[2];
+    const float sigma = pick_taps<F, 2, REUSE>(x, u, idx);
+    tap = make_int4(idx[0], idx[1], 0, L);
+    const int cx = min(max(idx[0], 0), W - 1), cy = min(max(idx[1], 0), H - 1);
+    TexelIO<FMT, C>::load(t.texels, t.level_off[L] + (int64_t)cy * W + cx, v);
+    if constexpr (!Filter<F>::NONNEG) {
+#pragma unroll
+      for (int c = 0; c < C; ++c) v[c] *= sigma;
+    }
   }
 }
 
@@ -174,6 +195,18 @@ __device__ __forceinline__ float dense_stochastic_one(const Dense3DView& g, cons
     return g.background;
   }
   const uint4 r = query_variates(a, j, sample);
+  if constexpr (F == STF_FILTER_CATMULL_ROM_POSITIVIZED) {
+    const uint4 r1 = query_variates(a, j, sample, 1u);
+    const float up[4] = {unit24(r.x), unit24(r.y), unit24(r.z), unit24(r.w)};
+    const float un[4] = {unit24(r1.x), unit24(r1.y), unit24(r1.z), unit24(r1.w)};
+    int ip[3], in[3];
+    float Wp, Wn;
+    pick_positivized<3>(x, up, un, ip, in, Wp, Wn);
+    tap = make_int4(ip[0], ip[1], ip[2], 0);
+    float t = Wp * dense_fetch<FMT>(g, ip[0], ip[1], ip[2]);
+    if (Wn > 0.0f) t = fmaf(-Wn, dense_fetch<FMT>(g, in[0], in[1], in[2]), t);
+    return t;
+  }
   const float u[3] = {unit24(r.x), unit24(r.y), unit24(r.z)};
   int idx[3];
   const float sigma = pick_taps<F, 3, REUSE>(x, u, idx);
@@ -287,6 +320,8 @@ cudaError_t launch_tex2d(Op op, int filter, int fmt, int channels, const Tex2DVi
     case STF_FILTER_BSPLINE3: return run_tex2d_f<STF_FILTER_BSPLINE3>(op, fmt, channels, t, a, s);
     case STF_FILTER_CATMULL_ROM:
       return run_tex2d_f<STF_FILTER_CATMULL_ROM>(op, fmt, channels, t, a, s);
+    case STF_FILTER_CATMULL_ROM_POSITIVIZED:
+      return run_tex2d_f<STF_FILTER_CATMULL_ROM_POSITIVIZED>(op, fmt, channels, t, a, s);
   }
   return cudaErrorInvalidValue;
 }
@@ -321,6 +356,8 @@ cudaError_t launch_dense3d(Op op, int filter, int fmt, const Dense3DView& g, con
     case STF_FILTER_LINEAR: return run_dense_f<STF_FILTER_LINEAR>(op, fmt, g, a, s);
     case STF_FILTER_BSPLINE3: return run_dense_f<STF_FILTER_BSPLINE3>(op, fmt, g, a, s);
     case STF_FILTER_CATMULL_ROM: return run_dense_f<STF_FILTER_CATMULL_ROM>(op, fmt, g, a, s);
+    case STF_FILTER_CATMULL_ROM_POSITIVIZED:
+      return run_dense_f<STF_FILTER_CATMULL_ROM_POSITIVIZED>(op, fmt, g, a, s);
   }
   return cudaErrorInvalidValue;
 }

@@ -303,6 +303,19 @@ __device__ __forceinline__ float sparse_stochastic_one(const SparseDev& g, const
     return g.background;
   }
   const uint4 r = query_variates(a, j, sample);
+  if constexpr (F == STF_FILTER_CATMULL_ROM_POSITIVIZED) {
+    const uint4 r1 = query_variates(a, j, sample, 1u);
+    const float up[4] = {unit24(r.x), unit24(r.y), unit24(r.z), unit24(r.w)};
+    const float un[4] = {unit24(r1.x), unit24(r1.y), unit24(r1.z), unit24(r1.w)};
+    int ip[3], in[3];
+    float Wp, Wn;
+    pick_positivized<3>(x, up, un, ip, in, Wp, Wn);
+    tap = make_int4(ip[0], ip[1], ip[2], 0);
+    float t = Wp * sparse_value<FMT>(g, sparse_leaf(g, su, ip[0], ip[1], ip[2]), ip[0], ip[1], ip[2]);
+    if (Wn > 0.0f)
+      t = fmaf(-Wn, sparse_value<FMT>(g, sparse_leaf(g, su, in[0], in[1], in[2]), in[0], in[1], in[2]), t);
+    return t;
+  }
   const float u[3] = {unit24(r.x), unit24(r.y), unit24(r.z)};
   int idx[3];
   const float sigma = pick_taps<F, 3, REUSE>(x, u, idx);
@@ -424,6 +437,8 @@ cudaError_t launch_sparse3d(Op op, int filter, int fmt, const SparseDev& g, cons
     case STF_FILTER_LINEAR: return run_sparse_f<STF_FILTER_LINEAR>(op, fmt, g, a, s);
     case STF_FILTER_BSPLINE3: return run_sparse_f<STF_FILTER_BSPLINE3>(op, fmt, g, a, s);
     case STF_FILTER_CATMULL_ROM: return run_sparse_f<STF_FILTER_CATMULL_ROM>(op, fmt, g, a, s);
+    case STF_FILTER_CATMULL_ROM_POSITIVIZED:
+      return run_sparse_f<STF_FILTER_CATMULL_ROM_POSITIVIZED>(op, fmt, g, a, s);
   }
   return cudaErrorInvalidValue;
 }

@@ -71,3 +71,42 @@ def check_deterministic(gpu_val, ref_val, scale):
 
 def to_dev(a):
     return torch.from_numpy(np.ascontiguousarray(a)).to(dev())
+
+
+def positivized_scale(xs32, tmax):
+    """(W+ + W-) * max|t| = prod_a sum|w_a| * max|t|: the magnitude the two-tap
+    estimate's rounding is relative to."""
+    s = 1.0
+    for x in xs32:
+        _, f, _ = filters.axis_frame(x)
+        s = s * np.sum(np.abs(filters.axis_weights(f, "catmull_rom")), axis=0)
+    return np.nan_to_num(s) * tmax
+
+
+def positivized_moments(fetch, xs32):
+    """Exact mean and variance of the positivized estimate (two independent draws)."""
+    D = len(xs32)
+    frames = [filters.axis_frame(x) for x in xs32]
+    w64 = [filters.axis_weights(f, "catmull_rom") for (_, f, _) in frames]
+    m = filters._block_masses(w64, D)
+    res = {}
+    for sign in (1, -1):
+        blocks = filters._blocks_of_sign(D, sign)
+        W = np.sum([m[b] for b in blocks], axis=0)
+        e1 = e2 = 0.0
+        for b in blocks:
+            pb = np.where(W > 0, m[b] / np.where(W > 0, W, 1), 0)
+            for combo in itertools.product((0, 1), repeat=D):
+                p, idx = pb.copy(), []
+                for a in range(D):
+                    t0, t1 = ((0, 3) if (b >> a) & 1 else (1, 2))
+                    tap = (t0, t1)[combo[a]]
+                    s = np.abs(w64[a][t0]) + np.abs(w64[a][t1])
+                    p = p * np.where(s > 0, np.abs(w64[a][tap]) / np.where(s > 0, s, 1), 0)
+                    idx.append(frames[a][0] - 1 + tap)
+                t = fetch(*idx)
+                e1 = e1 + p[:, None] * t
+                e2 = e2 + p[:, None] * t * t
+        res[sign] = (W[:, None], e1, e2)
+    (Wp, p1, p2), (Wn, n1, n2) = res[1], res[-1]
+    return Wp * p1 - Wn * n1, Wp ** 2 * (p2 - p1 ** 2) + Wn ** 2 * (n2 - n1 ** 2)

@@ -6,8 +6,8 @@ import torch
 import paper_2305_05810_gb300 as stf
 import synth
 from oracle import filters, textures
-from parity import (abs_weighted_sum, check_deterministic, check_stochastic, dev, quantise,
-                    to_dev)
+from parity import (abs_weighted_sum, check_deterministic, check_stochastic, dev,
+                    positivized_moments, positivized_scale, quantise, to_dev)
 
 pytestmark = pytest.mark.gpu
 FILTERS = ["linear", "bspline3", "catmull_rom"]
@@ -240,3 +240,73 @@ def test_full_size_dense_ray_march_sampled():
     dv, _, _ = filters.lookup_3d(ref, q[idx], "bspline3", stochastic_form=False)
     check_deterministic(det.cpu().numpy()[idx], dv, 0.0)
     stf.stf_synchronize(T.handle)
+
+
+def _check_positivized(gpu_val, gpu_taps, rv, rt, ex, scale):
+    gpu_val = np.asarray(gpu_val, dtype=np.float64).reshape(rv.shape)
+    same = np.all(np.asarray(gpu_taps).reshape(-1, 4) == rt, axis=1)
+    assert np.all(same | ex), np.nonzero(~(same | ex))[0][:5]
+    ok = same & ~ex
+    err = np.abs(gpu_val - rv)[ok]
+    lim = 2e-6 * (np.abs(rv[ok]) + scale[ok, None])
+    assert np.all(err <= lim), np.max(err - lim)
+
+
+def test_positivized_tex2d_matches_oracle():
+    tex, uv = _c1()
+    T = stf.Texture(stf.KIND_TEX2D, tex, dims=(256, 256, 1), channels=4)
+    n = uv.shape[0]
+    taps = torch.empty((n, 4), dtype=torch.int32, device=dev())
+    out = T.lookup(to_dev(uv), taps=taps, filter="catmull_rom_positivized", seed=21)
+    ref = textures.Texture2D([tex.astype(np.float64)])
+    rv, rt, ex = filters.lookup_2d(ref, uv, None, "catmull_rom_positivized", stochastic_form=True, seed=21)
+    torch.cuda.synchronize()
+    x = (uv[:, 0] * np.float32(256) - np.float32(0.5)).astype(np.float32)
+    y = (uv[:, 1] * np.float32(256) - np.float32(0.5)).astype(np.float32)
+    _check_positivized(out.cpu().numpy(), taps.cpu().numpy(), rv, rt, ex,
+                       positivized_scale([x, y], float(np.max(np.abs(tex)))))
+    det = T.lookup_deterministic(to_dev(uv), filter="catmull_rom_positivized")
+    det_cr = T.lookup_deterministic(to_dev(uv), filter="catmull_rom")
+    assert torch.equal(det, det_cr)
+
+
+@pytest.mark.parametrize("fmt", [stf.FMT_F32, stf.FMT_F16])
+def test_positivized_dense_matches_oracle(fmt):
+    vals, pts = _dense()
+    n = vals.shape[0]
+    T = stf.Texture(stf.KIND_DENSE3D, vals, dims=(n, n, n), fmt=fmt)
+    ref = textures.Dense3D(quantise(vals, fmt))
+    N = pts.shape[0]
+    taps = torch.empty((N, 4), dtype=torch.int32, device=dev())
+    out = T.lookup(to_dev(pts), taps=taps, filter="catmull_rom_positivized", seed=5)
+    rv, rt, ex = filters.lookup_3d(ref, pts, "catmull_rom_positivized", stochastic_form=True, seed=5)
+    torch.cuda.synchronize()
+    _check_positivized(out.cpu().numpy(), taps.cpu().numpy(), rv, rt, ex,
+                       positivized_scale([pts[:, 0], pts[:, 1], pts[:, 2]], float(np.max(vals))))
+
+
+def test_positivized_unbiased_and_lower_variance_c1():
+    """4096 samples per query: z-scores of the positivized mean against the
+    deterministic filter with its exact variance; its sample variance is below the
+    one-tap estimator's on average."""
+    tex, uv = _c1()
+    uv = uv[:16384]
+    T = stf.Texture(stf.KIND_TEX2D, tex, dims=(256, 256, 1), channels=4)
+    S = 4096
+    s, s2 = T.accumulate(to_dev(uv), S, filter="catmull_rom_positivized", seed=44)
+    s_cr, s2_cr = T.accumulate(to_dev(uv), S, filter="catmull_rom", seed=44)
+    s, s2, s_cr, s2_cr = s.cpu().numpy(), s2.cpu().numpy(), s_cr.cpu().numpy(), s2_cr.cpu().numpy()
+    ref = textures.Texture2D([tex.astype(np.float64)])
+    x = (uv[:, 0] * np.float32(256) - np.float32(0.5)).astype(np.float32)
+    y = (uv[:, 1] * np.float32(256) - np.float32(0.5)).astype(np.float32)
+    F, var = positivized_moments(lambda ix, iy: ref.fetch(np.zeros_like(ix), ix, iy), [x, y])
+    mean = s / S
+    for c in range(4):
+        live = var[:, c] > 1e-18
+        z = (mean[live, c] - F[live, c]) / np.sqrt(var[live, c] / S)
+        assert np.mean(np.abs(z) > 3) <= 0.005
+        pooled = np.sum(mean[live, c] - F[live, c]) / np.sqrt(np.sum(var[live, c]) / S)
+        assert abs(pooled) <= 4.0
+    v_pos = np.mean(s2 / S - (s / S) ** 2)
+    v_cr = np.mean(s2_cr / S - (s_cr / S) ** 2)
+    assert v_pos < v_cr

@@ -189,3 +189,22 @@ def test_full_size_sparse_ray_march_sampled():
         T.close()
         del taps, sto, det
         torch.cuda.empty_cache()
+
+
+def test_positivized_sparse_matches_oracle():
+    from parity import positivized_scale
+    origins, values = synth.sparse_cloud(domain=256, seed=4)
+    T, ref = sparse_pair(origins, values, stf.FMT_F32)
+    pts = (origins[np.arange(30000) % len(origins)]
+           + synth.uniform(90000, 14).reshape(-1, 3) * np.float32(8)).astype(np.float32)
+    N = pts.shape[0]
+    taps = torch.empty((N, 4), dtype=torch.int32, device=dev())
+    out = T.lookup(to_dev(pts), taps=taps, filter="catmull_rom_positivized", seed=8)
+    rv, rt, ex = filters.lookup_3d(ref, pts, "catmull_rom_positivized", stochastic_form=True, seed=8)
+    torch.cuda.synchronize()
+    same = np.all(taps.cpu().numpy() == rt, axis=1)
+    assert np.all(same | ex)
+    ok = same & ~ex
+    scale = positivized_scale([pts[:, 0], pts[:, 1], pts[:, 2]], float(np.max(values)))
+    err = np.abs(out.cpu().numpy().astype(np.float64) - rv)[ok]
+    assert np.all(err <= 2e-6 * (np.abs(rv[ok]) + scale[ok, None]))
