@@ -11,11 +11,14 @@ Modules (each cites the passage of the paper it follows):
 * ``codecs``   -- binary16 and E4M3 storage formats.
 * ``textures`` -- texel stores: 2D MIP pyramids, dense and sparse 3D grids.
 * ``filters``  -- deterministic (Eq. 2, Eq. 9) and stochastic (Eq. 3, sampling
-  arrays of Section 2.2) lookups, and the exact expectation by enumeration.
+  arrays of Section 2.2) lookups, positivization, and the exact expectation by
+  enumeration.
+* ``fis``      -- filter importance sampling (Section 3): B-splines by sums of
+  uniforms, the Gaussian by Box-Muller, nearest-texel lookup.
 * ``mlp``      -- float64 forward and backward of the neural-texture decoder.
 
 Every function is pinned by a test in ``tests/test_oracle_*.py`` against something
 other than itself (closed forms, brute force, an independent library, or a value
 the paper prints).
 """
-from . import philox, kernels, codecs, textures, filters  # noqa: F401
+from . import philox, kernels, codecs, textures, fis, filters  # noqa: F401

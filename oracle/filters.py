@@ -37,6 +37,7 @@ Readings where the paper is silent or inconsistent (all stated in the design not
 import itertools
 import numpy as np
 
+from . import fis
 from .kernels import FILTERS
 from .philox import query_variates
 
@@ -309,9 +310,14 @@ def _raster(uv32, tex, L):
     return x, y
 
 
+def _fis_streams(qid, sample_index, seed, filt):
+    return [query_variates(qid, sample_index, seed, stream=j) for j in range(fis.STREAMS[filt])]
+
+
 def lookup_2d(tex, uv, lod, filt, *, stochastic_form, level_mode=LEVEL_STOCHASTIC,
-              qid=None, sample_index=0, seed=0, reuse=False):
-    """2D (MIP-mapped) lookup.  Returns (values (N, C), taps (N, 4) int, exempt)."""
+              qid=None, sample_index=0, seed=0, reuse=False, width=None):
+    """2D (MIP-mapped) lookup.  Returns (values (N, C), taps (N, 4) int, exempt).
+    width: the Gaussian's sigma in texels of the chosen level (fis_gaussian)."""
     uv32 = np.asarray(uv, dtype=np.float32).reshape(-1, 2)
     N = uv32.shape[0]
     lod32 = None if lod is None else np.asarray(lod, dtype=np.float32)
@@ -334,8 +340,23 @@ def lookup_2d(tex, uv, lod, filt, *, stochastic_form, level_mode=LEVEL_STOCHASTI
         taps[:, 0], taps[:, 1], taps[:, 3] = idx[0], idx[1], L0
         taps[~fin] = (0, 0, 0, -1)
         return val, taps, (exempt | ex) & fin
+    if stochastic_form and filt.startswith("fis_"):
+        x, y = _raster(uv32, tex, L0)
+        val, idx, ex, fin = fis.stochastic(lambda ix, iy: tex.fetch(L0, ix, iy), [x, y], filt,
+                                           _fis_streams(qid, sample_index, seed, filt), width)
+        fin &= ~bad_lod
+        val[~fin] = 0.0
+        taps[:, 0], taps[:, 1], taps[:, 3] = idx[0], idx[1], L0
+        taps[~fin] = (0, 0, 0, -1)
+        return val, taps, (exempt | ex) & fin
     if filt == "catmull_rom_positivized":
         filt = "catmull_rom"          # the deterministic twin is the Catmull-Rom filter
+    if filt.startswith("fis_"):
+        filt = fis.FIS_TWIN[filt]     # the filter that FIS applies
+    if filt == "gaussian":
+        det = lambda L, xs: fis.deterministic_gaussian(lambda ix, iy: tex.fetch(L, ix, iy), xs, width)
+    else:
+        det = lambda L, xs: deterministic(lambda ix, iy: tex.fetch(L, ix, iy), xs, filt)
     if stochastic_form:
         x, y = _raster(uv32, tex, L0)
         val, idx, ex, fin = stochastic(lambda ix, iy: tex.fetch(L0, ix, iy), [x, y], filt,
@@ -346,20 +367,35 @@ def lookup_2d(tex, uv, lod, filt, *, stochastic_form, level_mode=LEVEL_STOCHASTI
         taps[~fin] = (0, 0, 0, -1)
         return val, taps, (exempt | ex) & fin
     x0, y0 = _raster(uv32, tex, L0)
-    v0 = deterministic(lambda ix, iy: tex.fetch(L0, ix, iy), [x0, y0], filt)
+    v0 = det(L0, [x0, y0])
     x1, y1 = _raster(uv32, tex, L1)
-    v1 = deterministic(lambda ix, iy: tex.fetch(L1, ix, iy), [x1, y1], filt)
+    v1 = det(L1, [x1, y1])
     val = (1.0 - a)[:, None] * v0 + a[:, None] * v1
     val[bad_lod] = 0.0
     return val, None, None
 
 
 def lookup_3d(grid, p, filt, *, stochastic_form, qid=None, sample_index=0, seed=0,
-              reuse=False):
+              reuse=False, width=None):
     """3D lookup in index space (dense or sparse grid)."""
     p32 = np.asarray(p, dtype=np.float32).reshape(-1, 3)
     N = p32.shape[0]
     xs = [p32[:, 0], p32[:, 1], p32[:, 2]]
+    if filt.startswith("fis_"):
+        if not stochastic_form:
+            twin = fis.FIS_TWIN[filt]
+            if twin == "gaussian":
+                return fis.deterministic_gaussian(grid.fetch, xs, width, grid.background), None, None
+            return deterministic(grid.fetch, xs, twin, grid.background), None, None
+        if qid is None:
+            qid = np.arange(N, dtype=np.uint64)
+        val, idx, ex, fin = fis.stochastic(grid.fetch, xs, filt,
+                                           _fis_streams(qid, sample_index, seed, filt), width,
+                                           grid.background)
+        taps = np.zeros((N, 4), dtype=np.int64)
+        taps[:, 0], taps[:, 1], taps[:, 2] = idx
+        taps[~fin] = (0, 0, 0, -1)
+        return val, taps, ex & fin
     if filt == "catmull_rom_positivized":
         if not stochastic_form:
             return deterministic(grid.fetch, xs, "catmull_rom", grid.background), None, None
