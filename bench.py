@@ -476,7 +476,19 @@ def run_ours(args):
         variants = [("deterministic_" + filt, deterministic(filt))]
         if w["name"] != "neural":
             variants += [("stochastic_catmull_rom", stochastic("catmull_rom")),
-                         ("stochastic_catmull_rom_positivized", stochastic("catmull_rom_positivized"))]
+                         ("stochastic_catmull_rom_positivized", stochastic("catmull_rom_positivized")),
+                         # filter importance sampling: B-splines by sums of uniforms, and a
+                         # Gaussian (sigma = 1 texel) by Box-Muller, each one texel fetch
+                         ("stochastic_fis_linear", stochastic("fis_linear")),
+                         ("stochastic_fis_bspline3", stochastic("fis_bspline3")),
+                         ("stochastic_fis_gaussian_sigma1", stochastic("fis_gaussian", width=1.0))]
+            # its deterministic twin sums every tap within 5.77 sigma (13 per axis), so it
+            # is timed on the first 2^20 queries
+            m = min(n, 1 << 20)
+            pg = stf.make_params("fis_gaussian", level_mode=level_mode, width=1.0)
+            det_g = (lambda: stf.stf_lookup_batch_deterministic(tex.handle, pg, coords, lod, m, out,
+                                                                stream))
+            variants += [("deterministic_fis_gaussian_sigma1_first_2^20", det_g)]
         if filt != "linear":
             variants += [("stochastic_linear", stochastic("linear")),
                          ("deterministic_linear", deterministic("linear"))]
@@ -497,7 +509,8 @@ def run_ours(args):
         for name, fn in variants:
             try:
                 p2, t2 = time_steps(torch, fn, max(3, args.steps // 2), 2, stream)
-                extras[name] = {"lookups_per_s": n * len(p2) / (t2 / 1000.0),
+                nq = min(n, 1 << 20) if name.endswith("first_2^20") else n
+                extras[name] = {"lookups_per_s": nq * len(p2) / (t2 / 1000.0),
                                 "ms_p50": pct(p2, 50), "ms_p99": pct(p2, 99)}
             except stf.StfError as e:
                 extras[name] = {"unavailable": str(e)}

@@ -77,13 +77,33 @@ typedef enum {
   STF_FILTER_BSPLINE3 = 1,   /* cubic B-spline K_bs, 4 taps per axis (Eq. 9) */
   STF_FILTER_CATMULL_ROM = 2, /* cubic K3 with a = -1/2 (Appendix A), 4 taps per axis;
                                  stochastic form: one tap by |w| with scale sign * sum|w| */
-  STF_FILTER_CATMULL_ROM_POSITIVIZED = 3 /* the same filter, stochastic form with
+  STF_FILTER_CATMULL_ROM_POSITIVIZED = 3, /* the same filter, stochastic form with
                                  positivization (Section 2.2; Appendix B): one tap from
                                  the positive and one from the negative weights,
                                  W+ t(j+) - W- t(j-); two texel fetches, lower variance.
                                  The deterministic form equals STF_FILTER_CATMULL_ROM.
                                  reuse_xi is ignored.  Not offered for neural textures. */
+  /* Filter importance sampling (Section 3, "Filter Importance Sampling"): a
+   * continuous offset s is drawn from a density and the texel nearest to x + s,
+   * floor(x + s + 1/2), is returned unscaled.  The nearest-texel step convolves the
+   * density with a unit box, which gives the filter each entry names.  reuse_xi is
+   * ignored; not offered for neural textures. */
+  STF_FILTER_FIS_LINEAR = 4,   /* s uniform on [-1/2, 1/2) per axis (one variate): the
+                                  tent filter K1.  Deterministic form: STF_FILTER_LINEAR */
+  STF_FILTER_FIS_BSPLINE3 = 5, /* s = sum of three uniforms on [-1/2, 1/2) per axis
+                                  (the quadratic B-spline density): the cubic B-spline.
+                                  Draws Philox streams 0, 1 and 2.  Deterministic form:
+                                  STF_FILTER_BSPLINE3 */
+  STF_FILTER_FIS_GAUSSIAN = 6  /* s = sigma * normal (Box-Muller on stream 0 words
+                                  (0, 1), and (2, 3) for the z axis), sigma =
+                                  params->filter_width in texels of the chosen level,
+                                  0 < sigma <= STF_FIS_MAX_WIDTH.  The filter is the
+                                  Gaussian convolved with the box; the deterministic
+                                  form sums it over every tap within 5.77 sigma (the
+                                  largest offset a 24-bit draw can make) */
 } stf_filter;
+
+#define STF_FIS_MAX_WIDTH 8.0f
 
 typedef enum {
   STF_LEVEL_NEAREST = 0,   /* level floor(lod + 1/2) in both forms */
@@ -134,7 +154,8 @@ typedef struct {
                              (same results, better gather locality) */
   int32_t reuse_xi;       /* 1: one variate carried across axes by the remapping
                              of Eq. 4 instead of one variate per axis */
-  int32_t reserved;
+  float filter_width;     /* STF_FILTER_FIS_GAUSSIAN: sigma in texels; ignored by the
+                             other filters */
 } stf_lookup_params;
 
 /* Create a device-resident texture from desc; queued on `stream`, and the call

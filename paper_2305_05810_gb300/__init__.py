@@ -26,8 +26,12 @@ KIND_TEX2D, KIND_DENSE3D, KIND_SPARSE3D, KIND_NEURAL2D = 0, 1, 2, 3
 NEURAL_LATENT, NEURAL_HIDDEN, NEURAL_OUT, NEURAL_PARAMS = 8, 64, 7, 5191
 FMT_F32, FMT_F16, FMT_E4M3_SCALED = 0, 1, 2
 FILTER_LINEAR, FILTER_BSPLINE3, FILTER_CATMULL_ROM, FILTER_CATMULL_ROM_POSITIVIZED = 0, 1, 2, 3
+FILTER_FIS_LINEAR, FILTER_FIS_BSPLINE3, FILTER_FIS_GAUSSIAN = 4, 5, 6
+FIS_MAX_WIDTH = 8.0                  # include/stf.h STF_FIS_MAX_WIDTH
 FILTERS = {"linear": FILTER_LINEAR, "bspline3": FILTER_BSPLINE3, "catmull_rom": FILTER_CATMULL_ROM,
-           "catmull_rom_positivized": FILTER_CATMULL_ROM_POSITIVIZED}
+           "catmull_rom_positivized": FILTER_CATMULL_ROM_POSITIVIZED,
+           "fis_linear": FILTER_FIS_LINEAR, "fis_bspline3": FILTER_FIS_BSPLINE3,
+           "fis_gaussian": FILTER_FIS_GAUSSIAN}
 LEVEL_NEAREST, LEVEL_STOCHASTIC = 0, 1
 STF_NOALLOC_MAX_QUERIES = 1 << 20   # include/stf.h
 
@@ -56,7 +60,7 @@ class LookupParams(ctypes.Structure):
     _fields_ = [("filter", ctypes.c_int32), ("level_mode", ctypes.c_int32),
                 ("seed", ctypes.c_uint64), ("query_offset", ctypes.c_uint64),
                 ("sample_index", ctypes.c_uint32), ("bin_queries", ctypes.c_int32),
-                ("reuse_xi", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("reuse_xi", ctypes.c_int32), ("filter_width", ctypes.c_float)]
 
 
 class NeuralDesc(ctypes.Structure):
@@ -212,11 +216,11 @@ def stf_synchronize(tex, stream=None):
 
 
 def make_params(filter="bspline3", seed=0, sample_index=0, query_offset=0, level_mode=LEVEL_STOCHASTIC,
-                bin_queries=False, reuse_xi=False):
+                bin_queries=False, reuse_xi=False, width=0.0):
     f = FILTERS[filter] if isinstance(filter, str) else int(filter)
     return LookupParams(filter=f, level_mode=level_mode, seed=seed, query_offset=query_offset,
                         sample_index=sample_index, bin_queries=int(bin_queries),
-                        reuse_xi=int(reuse_xi))
+                        reuse_xi=int(reuse_xi), filter_width=float(width))
 
 
 class Texture:

@@ -279,10 +279,14 @@ stf_status check_lookup(stf_texture t, const stf_lookup_params* p, const float* 
   if (!handle_ok(t)) return fail(STF_ERR_INVALID_HANDLE, "unknown texture handle");
   if (!p) return fail(STF_ERR_INVALID_ARGUMENT, "params is NULL");
   if (n < 0) return fail(STF_ERR_INVALID_ARGUMENT, "n < 0");
-  if (p->filter < STF_FILTER_LINEAR || p->filter > STF_FILTER_CATMULL_ROM_POSITIVIZED)
+  if (p->filter < STF_FILTER_LINEAR || p->filter > STF_FILTER_FIS_GAUSSIAN)
     return fail(STF_ERR_INVALID_ARGUMENT, "unknown filter %d", p->filter);
-  if (p->filter == STF_FILTER_CATMULL_ROM_POSITIVIZED && t->kind == STF_KIND_NEURAL2D)
-    return fail(STF_ERR_UNSUPPORTED, "positivized filtering is not offered for neural textures");
+  if (p->filter >= STF_FILTER_CATMULL_ROM_POSITIVIZED && t->kind == STF_KIND_NEURAL2D)
+    return fail(STF_ERR_UNSUPPORTED, "filter %d is not offered for neural textures", p->filter);
+  if (p->filter == STF_FILTER_FIS_GAUSSIAN &&
+      !(p->filter_width > 0.0f && p->filter_width <= STF_FIS_MAX_WIDTH))
+    return fail(STF_ERR_INVALID_ARGUMENT, "filter_width %g outside (0, %g]", (double)p->filter_width,
+                (double)STF_FIS_MAX_WIDTH);
   if (p->level_mode != STF_LEVEL_NEAREST && p->level_mode != STF_LEVEL_STOCHASTIC)
     return fail(STF_ERR_INVALID_ARGUMENT, "unknown level mode %d", p->level_mode);
   if (n == 0) return STF_OK;
@@ -312,6 +316,7 @@ LookupArgs make_args(const stf_lookup_params* p, const float* coords, const floa
   a.sample_index = p->sample_index;
   a.reuse = p->reuse_xi != 0;
   a.level_mode = p->level_mode;
+  a.width = p->filter == STF_FILTER_FIS_GAUSSIAN ? p->filter_width : 0.0f;
   return a;
 }
 

@@ -198,6 +198,7 @@ struct LookupArgs {
   uint32_t sample_index;
   int32_t reuse;
   int32_t level_mode;
+  float width;            // Gaussian FIS: sigma in texels
   int32_t n_samples;      // accumulate kernels
   double* sum;
   double* sumsq;
@@ -279,6 +280,130 @@ __device__ __forceinline__ void pick_positivized(const float* x, const float* up
     }
     if (set) Wn = acc; else Wp = acc;
   }
+}
+
+// ---------------------------------------------------------------- filter importance sampling
+// Section 3, "Filter Importance Sampling": an offset s is drawn from a density and
+// the texel nearest to x + s, floor(x + s + 1/2), is fetched unscaled.  Taking the
+// nearest texel convolves the density with a unit box; that convolution is the
+// filter applied (a B-spline of one degree higher, or the box-blurred Gaussian).
+template <int F>
+struct IsFis {
+  static constexpr bool value = F == STF_FILTER_FIS_LINEAR || F == STF_FILTER_FIS_BSPLINE3 ||
+                                F == STF_FILTER_FIS_GAUSSIAN;
+};
+
+// Filters whose stochastic form can carry one variate across axes (Eq. 4).
+template <int F>
+struct UsesReuse {
+  static constexpr bool value = !IsFis<F>::value && F != STF_FILTER_CATMULL_ROM_POSITIVIZED;
+};
+
+// Deterministic forms of the B-spline FIS filters: the filters they apply.
+template <> struct Filter<STF_FILTER_FIS_LINEAR> : Filter<STF_FILTER_LINEAR> {};
+template <> struct Filter<STF_FILTER_FIS_BSPLINE3> : Filter<STF_FILTER_BSPLINE3> {};
+
+// B-splines: s is the sum of n uniforms on [-1/2, 1/2), so the index is
+// floor(x + sum u - (n - 1)/2).  With u = k 2^-24 (24-bit integers k) and x 2^24 exact
+// in float32 (|x| <= 2^24), it is formed exactly in 64-bit integers as
+// (floor(x 2^24) + sum k - (n - 1) 2^23) >> 24 (arithmetic shift = floor division).
+__device__ __forceinline__ int fis_bspline_index(float x, uint32_t ksum, int n) {
+  const long long X = __float2ll_rd(__fmul_rn(x, 16777216.0f));
+  return (int)((X + (long long)ksum - (long long)(n - 1) * 8388608LL) >> 24);
+}
+
+// Gaussian: Box-Muller radius sigma sqrt(-2 ln(1 - u)); 1 - u is exact and positive
+// for a 24-bit u, so the largest radius is sigma sqrt(48 ln 2) = 5.7683 sigma.
+__device__ __forceinline__ float bm_radius(float u, float sigma) {
+  return sigma * sqrtf(-2.0f * logf(1.0f - u));
+}
+
+// floor(x + s + 1/2) as floor(x) + floor(frac(x) + s + 1/2), which keeps the float32
+// sum small.
+__device__ __forceinline__ int fis_nearest(float x, float s) {
+  float f;
+  const int b = axis_base(x, f);
+  return b + (int)floorf(__fadd_rn(__fadd_rn(f, s), 0.5f));
+}
+
+// Tap of each axis for the FIS filters.  Variates: B-spline uniform j of axis a is
+// word a of Philox stream j; the Gaussian takes the Box-Muller pair (word 0, word 1)
+// of stream 0 for x and y, and (word 2, word 3) for z.  r0 is stream 0.
+template <int F, int D>
+__device__ __forceinline__ void pick_fis(const float* x, const LookupArgs& a, int64_t j,
+                                         uint32_t sample, const uint4& r0, int* idx) {
+  const uint32_t w0[4] = {r0.x, r0.y, r0.z, r0.w};
+  if constexpr (F == STF_FILTER_FIS_GAUSSIAN) {
+    const float r = bm_radius(unit24(r0.x), a.width);
+    float sn, cs;
+    sincospif(2.0f * unit24(r0.y), &sn, &cs);
+    idx[0] = fis_nearest(x[0], r * cs);
+    idx[1] = fis_nearest(x[1], r * sn);
+    if constexpr (D == 3) idx[2] = fis_nearest(x[2], bm_radius(unit24(r0.z), a.width) *
+                                                         cospif(2.0f * unit24(r0.w)));
+  } else if constexpr (F == STF_FILTER_FIS_LINEAR) {
+#pragma unroll
+    for (int d = 0; d < D; ++d) idx[d] = fis_bspline_index(x[d], w0[d] >> 8, 1);
+  } else {
+    const uint4 r1 = query_variates(a, j, sample, 1u), r2 = query_variates(a, j, sample, 2u);
+    const uint32_t w1[4] = {r1.x, r1.y, r1.z, r1.w}, w2[4] = {r2.x, r2.y, r2.z, r2.w};
+#pragma unroll
+    for (int d = 0; d < D; ++d)
+      idx[d] = fis_bspline_index(x[d], (w0[d] >> 8) + (w1[d] >> 8) + (w2[d] >> 8), 3);
+  }
+}
+
+// Deterministic form of the Gaussian FIS filter, one axis: taps lo..hi, the nearest
+// texels of x -+ 5.7683 sigma (every tap a 24-bit draw can reach), with weights
+// (erf((i + 1/2 - x) k) - erf((i - 1/2 - x) k)) / 2, k = 1 / (sigma sqrt 2): the
+// Gaussian convolved with the unit box.  The mass beyond the window is below 1e-8.
+struct GaussAxis {
+  int lo, hi;
+  float x, k;
+};
+
+__device__ __forceinline__ GaussAxis gauss_axis(float x, float sigma) {
+  GaussAxis g;
+  const float R = 5.7683466f * sigma;
+  g.lo = (int)floorf(__fadd_rn(__fsub_rn(x, R), 0.5f));
+  g.hi = (int)floorf(__fadd_rn(__fadd_rn(x, R), 0.5f));
+  g.x = x;
+  g.k = 0.70710678f / sigma;
+  return g;
+}
+
+// Edge value erf((e - x) k) at e = i - 1/2; consecutive taps share their edges.
+__device__ __forceinline__ float gauss_edge(const GaussAxis& g, int i) {
+  return erff(__fsub_rn((float)i - 0.5f, g.x) * g.k);
+}
+
+// Sum over the D-dimensional Gaussian window of prod_a w_a(i_a) * fetch(i).  Each
+// axis walks its taps carrying the shared edge value, so a tap costs one erf per
+// axis.
+template <class Fetch>
+__device__ __forceinline__ float gauss_window_sum3(const float* x, float sigma, Fetch fetch) {
+  const GaussAxis gx = gauss_axis(x[0], sigma), gy = gauss_axis(x[1], sigma),
+                  gz = gauss_axis(x[2], sigma);
+  float acc = 0.0f;
+  float ez0 = gauss_edge(gz, gz.lo);
+  for (int iz = gz.lo; iz <= gz.hi; ++iz) {
+    const float ez1 = gauss_edge(gz, iz + 1);
+    const float wz = 0.5f * (ez1 - ez0);
+    ez0 = ez1;
+    float ey0 = gauss_edge(gy, gy.lo);
+    for (int iy = gy.lo; iy <= gy.hi; ++iy) {
+      const float ey1 = gauss_edge(gy, iy + 1);
+      const float wyz = 0.5f * (ey1 - ey0) * wz;
+      ey0 = ey1;
+      float ex0 = gauss_edge(gx, gx.lo);
+      for (int ix = gx.lo; ix <= gx.hi; ++ix) {
+        const float ex1 = gauss_edge(gx, ix + 1);
+        acc = fmaf(0.5f * (ex1 - ex0) * wyz, fetch(ix, iy, iz), acc);
+        ex0 = ex1;
+      }
+    }
+  }
+  return acc;
 }
 
 template <int FMT, int C> struct TexelIO;

@@ -38,7 +38,13 @@ __device__ __forceinline__ void tex2d_stochastic_one(const Tex2DView& t, const L
     tap = make_int4(0, 0, 0, -1);
     return;
   }
-  if constexpr (F == STF_FILTER_CATMULL_ROM_POSITIVIZED) {
+  if constexpr (IsFis<F>::value) {
+    int idx[2];
+    pick_fis<F, 2>(x, a, j, sample, r, idx);
+    tap = make_int4(idx[0], idx[1], 0, L);
+    TexelIO<FMT, C>::load(t.texels, t.level_off[L] + (int64_t)min(max(idx[1], 0), H - 1) * W +
+                                        min(max(idx[0], 0), W - 1), v);
+  } else if constexpr (F == STF_FILTER_CATMULL_ROM_POSITIVIZED) {
     const uint4 r1 = query_variates(a, j, sample, 1u);
     const float up[3] = {unit24(r.x), unit24(r.y), unit24(r.z)};
     const float un[3] = {unit24(r1.x), unit24(r1.y), unit24(r1.z)};
@@ -73,12 +79,33 @@ __device__ __forceinline__ void tex2d_stochastic_one(const Tex2DView& t, const L
 
 template <int F, int FMT, int C>
 __device__ __forceinline__ void tex2d_det_level(const Tex2DView& t, int L, float2 uv, float scale,
-                                                float* acc) {
+                                                float width, float* acc) {
   using Fl = Filter<F>;
   const int W = t.level_w[L], H = t.level_h[L];
   float x[2] = {__fsub_rn(__fmul_rn(uv.x, (float)W), 0.5f),
                 __fsub_rn(__fmul_rn(uv.y, (float)H), 0.5f)};
   if (!prepare_coords<2>(x)) return;
+  if constexpr (F == STF_FILTER_FIS_GAUSSIAN) {
+    const GaussAxis gx = gauss_axis(x[0], width), gy = gauss_axis(x[1], width);
+    float ey0 = gauss_edge(gy, gy.lo);
+    for (int iy = gy.lo; iy <= gy.hi; ++iy) {
+      const float ey1 = gauss_edge(gy, iy + 1);
+      const float wy = 0.5f * (ey1 - ey0) * scale;
+      ey0 = ey1;
+      const int64_t row = t.level_off[L] + (int64_t)min(max(iy, 0), H - 1) * W;
+      float ex0 = gauss_edge(gx, gx.lo);
+      for (int ix = gx.lo; ix <= gx.hi; ++ix) {
+        const float ex1 = gauss_edge(gx, ix + 1);
+        const float w = 0.5f * (ex1 - ex0) * wy;
+        ex0 = ex1;
+        float tv[C];
+        TexelIO<FMT, C>::load(t.texels, row + min(max(ix, 0), W - 1), tv);
+#pragma unroll
+        for (int c = 0; c < C; ++c) acc[c] = fmaf(w, tv[c], acc[c]);
+      }
+    }
+    return;
+  } else {
   float fx, fy;
   const int bx = axis_base(x[0], fx) + Fl::OFF0, by = axis_base(x[1], fy) + Fl::OFF0;
   float wx[Fl::T], wy[Fl::T];
@@ -100,6 +127,7 @@ __device__ __forceinline__ void tex2d_det_level(const Tex2DView& t, int L, float
 #pragma unroll
       for (int c = 0; c < C; ++c) acc[c] = fmaf(w, tv[c], acc[c]);
     }
+  }
   }
 }
 
@@ -127,18 +155,18 @@ __global__ void __launch_bounds__(256) k_tex2d_deterministic(Tex2DView t, Lookup
     for (int c = 0; c < C; ++c) acc[c] = 0.0f;
     if (isfinite(lod)) {
       if (a.lod == nullptr || t.levels <= 1) {
-        tex2d_det_level<F, FMT, C>(t, 0, uv, 1.0f, acc);
+        tex2d_det_level<F, FMT, C>(t, 0, uv, 1.0f, a.width, acc);
       } else {
         const float lc = fminf(fmaxf(lod, 0.0f), (float)(t.levels - 1));
         if (a.level_mode == STF_LEVEL_NEAREST) {
           tex2d_det_level<F, FMT, C>(t, min((int)floorf(__fadd_rn(lc, 0.5f)), t.levels - 1), uv,
-                                     1.0f, acc);
+                                     1.0f, a.width, acc);
         } else {
           const float fl = floorf(lc);
           const float frac = __fsub_rn(lc, fl);
           const int L0 = (int)fl, L1 = min(L0 + 1, t.levels - 1);
-          tex2d_det_level<F, FMT, C>(t, L0, uv, 1.0f - frac, acc);
-          if (frac > 0.0f) tex2d_det_level<F, FMT, C>(t, L1, uv, frac, acc);
+          tex2d_det_level<F, FMT, C>(t, L0, uv, 1.0f - frac, a.width, acc);
+          if (frac > 0.0f) tex2d_det_level<F, FMT, C>(t, L1, uv, frac, a.width, acc);
         }
       }
     }
@@ -195,7 +223,12 @@ __device__ __forceinline__ float dense_stochastic_one(const Dense3DView& g, cons
     return g.background;
   }
   const uint4 r = query_variates(a, j, sample);
-  if constexpr (F == STF_FILTER_CATMULL_ROM_POSITIVIZED) {
+  if constexpr (IsFis<F>::value) {
+    int idx[3];
+    pick_fis<F, 3>(x, a, j, sample, r, idx);
+    tap = make_int4(idx[0], idx[1], idx[2], 0);
+    return dense_fetch<FMT>(g, idx[0], idx[1], idx[2]);
+  } else if constexpr (F == STF_FILTER_CATMULL_ROM_POSITIVIZED) {
     const uint4 r1 = query_variates(a, j, sample, 1u);
     const float up[4] = {unit24(r.x), unit24(r.y), unit24(r.z), unit24(r.w)};
     const float un[4] = {unit24(r1.x), unit24(r1.y), unit24(r1.z), unit24(r1.w)};
@@ -206,14 +239,15 @@ __device__ __forceinline__ float dense_stochastic_one(const Dense3DView& g, cons
     float t = Wp * dense_fetch<FMT>(g, ip[0], ip[1], ip[2]);
     if (Wn > 0.0f) t = fmaf(-Wn, dense_fetch<FMT>(g, in[0], in[1], in[2]), t);
     return t;
+  } else {
+    const float u[3] = {unit24(r.x), unit24(r.y), unit24(r.z)};
+    int idx[3];
+    const float sigma = pick_taps<F, 3, REUSE>(x, u, idx);
+    tap = make_int4(idx[0], idx[1], idx[2], 0);
+    float t = dense_fetch<FMT>(g, idx[0], idx[1], idx[2]);
+    if constexpr (!Filter<F>::NONNEG) t *= sigma;
+    return t;
   }
-  const float u[3] = {unit24(r.x), unit24(r.y), unit24(r.z)};
-  int idx[3];
-  const float sigma = pick_taps<F, 3, REUSE>(x, u, idx);
-  tap = make_int4(idx[0], idx[1], idx[2], 0);
-  float t = dense_fetch<FMT>(g, idx[0], idx[1], idx[2]);
-  if constexpr (!Filter<F>::NONNEG) t *= sigma;
-  return t;
 }
 
 template <int F, int FMT, bool REUSE>
@@ -235,22 +269,28 @@ __global__ void __launch_bounds__(256) k_dense_deterministic(Dense3DView g, Look
     float x[3] = {__ldg(a.coords + 3 * i), __ldg(a.coords + 3 * i + 1), __ldg(a.coords + 3 * i + 2)};
     float acc = g.background;
     if (prepare_coords<3>(x)) {
-      float fx, fy, fz;
-      const int bx = axis_base(x[0], fx) + Fl::OFF0, by = axis_base(x[1], fy) + Fl::OFF0,
-                bz = axis_base(x[2], fz) + Fl::OFF0;
-      float wx[Fl::T], wy[Fl::T], wz[Fl::T];
-      Fl::weights(fx, wx);
-      Fl::weights(fy, wy);
-      Fl::weights(fz, wz);
-      acc = 0.0f;
+      if constexpr (F == STF_FILTER_FIS_GAUSSIAN) {
+        acc = gauss_window_sum3(x, a.width, [&](int ix, int iy, int iz) {
+          return dense_fetch<FMT>(g, ix, iy, iz);
+        });
+      } else {
+        float fx, fy, fz;
+        const int bx = axis_base(x[0], fx) + Fl::OFF0, by = axis_base(x[1], fy) + Fl::OFF0,
+                  bz = axis_base(x[2], fz) + Fl::OFF0;
+        float wx[Fl::T], wy[Fl::T], wz[Fl::T];
+        Fl::weights(fx, wx);
+        Fl::weights(fy, wy);
+        Fl::weights(fz, wz);
+        acc = 0.0f;
 #pragma unroll
-      for (int kz = 0; kz < Fl::T; ++kz) {
+        for (int kz = 0; kz < Fl::T; ++kz) {
 #pragma unroll
-        for (int ky = 0; ky < Fl::T; ++ky) {
-          const float wyz = wy[ky] * wz[kz];
+          for (int ky = 0; ky < Fl::T; ++ky) {
+            const float wyz = wy[ky] * wz[kz];
 #pragma unroll
-          for (int kx = 0; kx < Fl::T; ++kx)
-            acc = fmaf(wx[kx] * wyz, dense_fetch<FMT>(g, bx + kx, by + ky, bz + kz), acc);
+            for (int kx = 0; kx < Fl::T; ++kx)
+              acc = fmaf(wx[kx] * wyz, dense_fetch<FMT>(g, bx + kx, by + ky, bz + kz), acc);
+          }
         }
       }
     }
@@ -281,13 +321,21 @@ static cudaError_t run_tex2d(Op op, const Tex2DView& t, const LookupArgs& a, cud
   const int threads = 256;
   const int blocks = grid_blocks(a.n, threads);
   if (op == OP_STOCHASTIC) {
-    if (a.reuse) k_tex2d_stochastic<F, FMT, C, true><<<blocks, threads, 0, s>>>(t, a);
-    else k_tex2d_stochastic<F, FMT, C, false><<<blocks, threads, 0, s>>>(t, a);
+    if constexpr (UsesReuse<F>::value) {
+      if (a.reuse) k_tex2d_stochastic<F, FMT, C, true><<<blocks, threads, 0, s>>>(t, a);
+      else k_tex2d_stochastic<F, FMT, C, false><<<blocks, threads, 0, s>>>(t, a);
+    } else {
+      k_tex2d_stochastic<F, FMT, C, false><<<blocks, threads, 0, s>>>(t, a);
+    }
   } else if (op == OP_DETERMINISTIC) {
     k_tex2d_deterministic<F, FMT, C><<<blocks, threads, 0, s>>>(t, a);
   } else {
-    if (a.reuse) k_tex2d_accumulate<F, FMT, C, true><<<blocks, threads, 0, s>>>(t, a);
-    else k_tex2d_accumulate<F, FMT, C, false><<<blocks, threads, 0, s>>>(t, a);
+    if constexpr (UsesReuse<F>::value) {
+      if (a.reuse) k_tex2d_accumulate<F, FMT, C, true><<<blocks, threads, 0, s>>>(t, a);
+      else k_tex2d_accumulate<F, FMT, C, false><<<blocks, threads, 0, s>>>(t, a);
+    } else {
+      k_tex2d_accumulate<F, FMT, C, false><<<blocks, threads, 0, s>>>(t, a);
+    }
   }
   return cudaGetLastError();
 }
@@ -322,6 +370,11 @@ cudaError_t launch_tex2d(Op op, int filter, int fmt, int channels, const Tex2DVi
       return run_tex2d_f<STF_FILTER_CATMULL_ROM>(op, fmt, channels, t, a, s);
     case STF_FILTER_CATMULL_ROM_POSITIVIZED:
       return run_tex2d_f<STF_FILTER_CATMULL_ROM_POSITIVIZED>(op, fmt, channels, t, a, s);
+    case STF_FILTER_FIS_LINEAR: return run_tex2d_f<STF_FILTER_FIS_LINEAR>(op, fmt, channels, t, a, s);
+    case STF_FILTER_FIS_BSPLINE3:
+      return run_tex2d_f<STF_FILTER_FIS_BSPLINE3>(op, fmt, channels, t, a, s);
+    case STF_FILTER_FIS_GAUSSIAN:
+      return run_tex2d_f<STF_FILTER_FIS_GAUSSIAN>(op, fmt, channels, t, a, s);
   }
   return cudaErrorInvalidValue;
 }
@@ -331,13 +384,21 @@ static cudaError_t run_dense(Op op, const Dense3DView& g, const LookupArgs& a, c
   const int threads = 256;
   const int blocks = grid_blocks(a.n, threads);
   if (op == OP_STOCHASTIC) {
-    if (a.reuse) k_dense_stochastic<F, FMT, true><<<blocks, threads, 0, s>>>(g, a);
-    else k_dense_stochastic<F, FMT, false><<<blocks, threads, 0, s>>>(g, a);
+    if constexpr (UsesReuse<F>::value) {
+      if (a.reuse) k_dense_stochastic<F, FMT, true><<<blocks, threads, 0, s>>>(g, a);
+      else k_dense_stochastic<F, FMT, false><<<blocks, threads, 0, s>>>(g, a);
+    } else {
+      k_dense_stochastic<F, FMT, false><<<blocks, threads, 0, s>>>(g, a);
+    }
   } else if (op == OP_DETERMINISTIC) {
     k_dense_deterministic<F, FMT><<<blocks, threads, 0, s>>>(g, a);
   } else {
-    if (a.reuse) k_dense_accumulate<F, FMT, true><<<blocks, threads, 0, s>>>(g, a);
-    else k_dense_accumulate<F, FMT, false><<<blocks, threads, 0, s>>>(g, a);
+    if constexpr (UsesReuse<F>::value) {
+      if (a.reuse) k_dense_accumulate<F, FMT, true><<<blocks, threads, 0, s>>>(g, a);
+      else k_dense_accumulate<F, FMT, false><<<blocks, threads, 0, s>>>(g, a);
+    } else {
+      k_dense_accumulate<F, FMT, false><<<blocks, threads, 0, s>>>(g, a);
+    }
   }
   return cudaGetLastError();
 }
@@ -358,6 +419,9 @@ cudaError_t launch_dense3d(Op op, int filter, int fmt, const Dense3DView& g, con
     case STF_FILTER_CATMULL_ROM: return run_dense_f<STF_FILTER_CATMULL_ROM>(op, fmt, g, a, s);
     case STF_FILTER_CATMULL_ROM_POSITIVIZED:
       return run_dense_f<STF_FILTER_CATMULL_ROM_POSITIVIZED>(op, fmt, g, a, s);
+    case STF_FILTER_FIS_LINEAR: return run_dense_f<STF_FILTER_FIS_LINEAR>(op, fmt, g, a, s);
+    case STF_FILTER_FIS_BSPLINE3: return run_dense_f<STF_FILTER_FIS_BSPLINE3>(op, fmt, g, a, s);
+    case STF_FILTER_FIS_GAUSSIAN: return run_dense_f<STF_FILTER_FIS_GAUSSIAN>(op, fmt, g, a, s);
   }
   return cudaErrorInvalidValue;
 }

@@ -303,7 +303,12 @@ __device__ __forceinline__ float sparse_stochastic_one(const SparseDev& g, const
     return g.background;
   }
   const uint4 r = query_variates(a, j, sample);
-  if constexpr (F == STF_FILTER_CATMULL_ROM_POSITIVIZED) {
+  if constexpr (IsFis<F>::value) {
+    int idx[3];
+    pick_fis<F, 3>(x, a, j, sample, r, idx);
+    tap = make_int4(idx[0], idx[1], idx[2], 0);
+    return sparse_value<FMT>(g, sparse_leaf(g, su, idx[0], idx[1], idx[2]), idx[0], idx[1], idx[2]);
+  } else if constexpr (F == STF_FILTER_CATMULL_ROM_POSITIVIZED) {
     const uint4 r1 = query_variates(a, j, sample, 1u);
     const float up[4] = {unit24(r.x), unit24(r.y), unit24(r.z), unit24(r.w)};
     const float un[4] = {unit24(r1.x), unit24(r1.y), unit24(r1.z), unit24(r1.w)};
@@ -315,14 +320,15 @@ __device__ __forceinline__ float sparse_stochastic_one(const SparseDev& g, const
     if (Wn > 0.0f)
       t = fmaf(-Wn, sparse_value<FMT>(g, sparse_leaf(g, su, in[0], in[1], in[2]), in[0], in[1], in[2]), t);
     return t;
+  } else {
+    const float u[3] = {unit24(r.x), unit24(r.y), unit24(r.z)};
+    int idx[3];
+    const float sigma = pick_taps<F, 3, REUSE>(x, u, idx);
+    tap = make_int4(idx[0], idx[1], idx[2], 0);
+    float t = sparse_value<FMT>(g, sparse_leaf(g, su, idx[0], idx[1], idx[2]), idx[0], idx[1], idx[2]);
+    if constexpr (!Filter<F>::NONNEG) t *= sigma;
+    return t;
   }
-  const float u[3] = {unit24(r.x), unit24(r.y), unit24(r.z)};
-  int idx[3];
-  const float sigma = pick_taps<F, 3, REUSE>(x, u, idx);
-  tap = make_int4(idx[0], idx[1], idx[2], 0);
-  float t = sparse_value<FMT>(g, sparse_leaf(g, su, idx[0], idx[1], idx[2]), idx[0], idx[1], idx[2]);
-  if constexpr (!Filter<F>::NONNEG) t *= sigma;
-  return t;
 }
 
 template <int F, int FMT, bool REUSE>
@@ -349,7 +355,13 @@ __global__ void __launch_bounds__(256) k_sparse_deterministic(SparseDev g, Looku
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += stride) {
     float x[3] = {__ldg(a.coords + 3 * i), __ldg(a.coords + 3 * i + 1), __ldg(a.coords + 3 * i + 2)};
     float acc = g.background;
-    if (prepare_coords<3>(x)) {
+    if constexpr (F == STF_FILTER_FIS_GAUSSIAN) {
+      // Every tap of the window is resolved on its own (root to leaf).
+      if (prepare_coords<3>(x))
+        acc = gauss_window_sum3(x, a.width, [&](int ix, int iy, int iz) {
+          return sparse_value<FMT>(g, sparse_leaf(g, su, ix, iy, iz), ix, iy, iz);
+        });
+    } else if (prepare_coords<3>(x)) {
       float fx, fy, fz;
       const int bx = axis_base(x[0], fx) + Fl::OFF0, by = axis_base(x[1], fy) + Fl::OFF0,
                 bz = axis_base(x[2], fz) + Fl::OFF0;
@@ -412,13 +424,21 @@ static cudaError_t run_sparse(Op op, const SparseDev& g, const LookupArgs& a, cu
   const int threads = 256;
   const int blocks = grid_blocks(a.n, threads);
   if (op == OP_STOCHASTIC) {
-    if (a.reuse) k_sparse_stochastic<F, FMT, true><<<blocks, threads, 0, s>>>(g, a);
-    else k_sparse_stochastic<F, FMT, false><<<blocks, threads, 0, s>>>(g, a);
+    if constexpr (UsesReuse<F>::value) {
+      if (a.reuse) k_sparse_stochastic<F, FMT, true><<<blocks, threads, 0, s>>>(g, a);
+      else k_sparse_stochastic<F, FMT, false><<<blocks, threads, 0, s>>>(g, a);
+    } else {
+      k_sparse_stochastic<F, FMT, false><<<blocks, threads, 0, s>>>(g, a);
+    }
   } else if (op == OP_DETERMINISTIC) {
     k_sparse_deterministic<F, FMT><<<blocks, threads, 0, s>>>(g, a);
   } else {
-    if (a.reuse) k_sparse_accumulate<F, FMT, true><<<blocks, threads, 0, s>>>(g, a);
-    else k_sparse_accumulate<F, FMT, false><<<blocks, threads, 0, s>>>(g, a);
+    if constexpr (UsesReuse<F>::value) {
+      if (a.reuse) k_sparse_accumulate<F, FMT, true><<<blocks, threads, 0, s>>>(g, a);
+      else k_sparse_accumulate<F, FMT, false><<<blocks, threads, 0, s>>>(g, a);
+    } else {
+      k_sparse_accumulate<F, FMT, false><<<blocks, threads, 0, s>>>(g, a);
+    }
   }
   return cudaGetLastError();
 }
@@ -439,6 +459,9 @@ cudaError_t launch_sparse3d(Op op, int filter, int fmt, const SparseDev& g, cons
     case STF_FILTER_CATMULL_ROM: return run_sparse_f<STF_FILTER_CATMULL_ROM>(op, fmt, g, a, s);
     case STF_FILTER_CATMULL_ROM_POSITIVIZED:
       return run_sparse_f<STF_FILTER_CATMULL_ROM_POSITIVIZED>(op, fmt, g, a, s);
+    case STF_FILTER_FIS_LINEAR: return run_sparse_f<STF_FILTER_FIS_LINEAR>(op, fmt, g, a, s);
+    case STF_FILTER_FIS_BSPLINE3: return run_sparse_f<STF_FILTER_FIS_BSPLINE3>(op, fmt, g, a, s);
+    case STF_FILTER_FIS_GAUSSIAN: return run_sparse_f<STF_FILTER_FIS_GAUSSIAN>(op, fmt, g, a, s);
   }
   return cudaErrorInvalidValue;
 }
