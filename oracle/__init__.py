@@ -15,10 +15,13 @@ Modules (each cites the passage of the paper it follows):
   enumeration.
 * ``fis``      -- filter importance sampling (Section 3): B-splines by sums of
   uniforms, the Gaussian by Box-Muller, nearest-texel lookup.
+* ``ewa``      -- anisotropic level of detail and (stochastic) EWA filtering
+  (Sections 5.2, 5.3; Appendix B).
 * ``mlp``      -- float64 forward and backward of the neural-texture decoder.
+* ``neural``   -- neural-texture lookups (latent fetch + decoder).
 
 Every function is pinned by a test in ``tests/test_oracle_*.py`` against something
 other than itself (closed forms, brute force, an independent library, or a value
 the paper prints).
 """
-from . import philox, kernels, codecs, textures, fis, filters  # noqa: F401
+from . import philox, kernels, codecs, textures, fis, filters, ewa  # noqa: F401
