@@ -17,6 +17,8 @@ Modules (each cites the passage of the paper it follows):
   uniforms, the Gaussian by Box-Muller, nearest-texel lookup.
 * ``ewa``      -- anisotropic level of detail and (stochastic) EWA filtering
   (Sections 5.2, 5.3; Appendix B).
+* ``dct``      -- DCT-compressed textures and stochastic triplanar mapping
+  (Section 5.2).
 * ``mlp``      -- float64 forward and backward of the neural-texture decoder.
 * ``neural``   -- neural-texture lookups (latent fetch + decoder).
 
@@ -24,4 +26,4 @@ Every function is pinned by a test in ``tests/test_oracle_*.py`` against somethi
 other than itself (closed forms, brute force, an independent library, or a value
 the paper prints).
 """
-from . import philox, kernels, codecs, textures, fis, filters, ewa  # noqa: F401
+from . import philox, kernels, codecs, textures, fis, filters, ewa, dct  # noqa: F401

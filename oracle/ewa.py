@@ -86,6 +86,18 @@ def footprint(W, H, grad, max_anisotropy):
     return (Mx, My), (mx, my), lod
 
 
+def footprint_finite(W, H, grad):
+    """Derivatives whose squared lengths in texels stay finite in float32 (others are
+    treated like non-finite input: background)."""
+    g = _f(grad)
+    out = np.all(np.isfinite(g), axis=1)
+    for a, b in ((0, 1), (2, 3)):
+        with np.errstate(over="ignore", invalid="ignore"):
+            l2 = _dot(_f(g[:, a] * F32(W)), _f(g[:, b] * F32(H)), _f(g[:, a] * F32(W)), _f(g[:, b] * F32(H)))
+        out &= np.isfinite(l2)
+    return out
+
+
 def ellipse(d0u, d0v, d1u, d1v):
     """Normalised (A, B, C) and the bounding-box half extents, float32 steps."""
     A = _f(_f(_f(d0v * d0v) + _f(d1v * d1v)) + F32(1))
@@ -120,6 +132,7 @@ def texels_and_weights(st_s, st_t, A, B, C, hs, ht):
     sums."""
     lut = weight_lut()
     s0 = int(np.ceil(_f(st_s - hs)))
+    assert np.ceil(_f(st_s + hs)) - s0 < 4096 and np.ceil(_f(st_t + ht)) - np.ceil(_f(st_t - ht)) < 4096
     s1 = int(np.floor(_f(st_s + hs)))
     t0 = int(np.ceil(_f(st_t - ht)))
     t1 = int(np.floor(_f(st_t + ht)))
@@ -151,6 +164,14 @@ def select(w, csum, u):
     exact = np.cumsum(w.astype(np.float64))
     d = np.min(np.abs(u - exact[:-1] / exact[-1])) if len(w) > 1 else 1.0
     return k, d
+
+
+def raster(uv, WL, HL):
+    """Raster position u W_L - 1/2, clamped to +-2^24 texels as in the other 2D lookups."""
+    lim = F32(1 << 24)
+    st_s = np.clip(_f(_f(uv[0] * F32(WL)) - F32(0.5)), -lim, lim)
+    st_t = np.clip(_f(_f(uv[1] * F32(HL)) - F32(0.5)), -lim, lim)
+    return F32(st_s), F32(st_t)
 
 
 EXEMPT_LEVEL = 4e-6     # log2 may differ by an ulp between float32 implementations
@@ -191,7 +212,7 @@ def lookup(tex, uv, grad, max_anisotropy, *, stochastic_form, level_mode=1, qid=
     val = np.zeros((N, C))
     taps = np.zeros((N, 4), dtype=np.int64)
     exempt = np.zeros(N, dtype=bool)
-    ok = np.all(np.isfinite(uv32), axis=1) & np.all(np.isfinite(g32), axis=1)
+    ok = np.all(np.isfinite(uv32), axis=1) & footprint_finite(W0, H0, g32)
     for q in range(N):
         if not ok[q]:
             taps[q] = (0, 0, 0, -1)
@@ -201,8 +222,7 @@ def lookup(tex, uv, grad, max_anisotropy, *, stochastic_form, level_mode=1, qid=
         parts = [(L0, 1.0 - frac)] if (stochastic_form or frac == 0.0) else [(L0, 1.0 - frac), (L1, frac)]
         for L, wl in parts:
             WL, HL = tex.size(L)
-            st_s = _f(_f(uv32[q, 0] * F32(WL)) - F32(0.5))
-            st_t = _f(_f(uv32[q, 1] * F32(HL)) - F32(0.5))
+            st_s, st_t = raster(uv32[q], WL, HL)
             d0u, d0v, d1u, d1v = level_axes(tex, L, (major[0][q:q + 1], major[1][q:q + 1]),
                                             (minor[0][q:q + 1], minor[1][q:q + 1]))
             A, B, Cc, hs, ht = ellipse(d0u[0], d0v[0], d1u[0], d1v[0])
@@ -235,8 +255,7 @@ def expectation(tex, uv, grad, max_anisotropy, level_mode=1, seed=0, sample_inde
     for q in range(N):
         L, _, _, _ = _levels(lod[q], nlev, level_mode, u[3][q], True)
         WL, HL = tex.size(L)
-        st_s = _f(_f(uv32[q, 0] * F32(WL)) - F32(0.5))
-        st_t = _f(_f(uv32[q, 1] * F32(HL)) - F32(0.5))
+        st_s, st_t = raster(uv32[q], WL, HL)
         d0u, d0v, d1u, d1v = level_axes(tex, L, (major[0][q:q + 1], major[1][q:q + 1]),
                                         (minor[0][q:q + 1], minor[1][q:q + 1]))
         A, B, Cc, hs, ht = ellipse(d0u[0], d0v[0], d1u[0], d1v[0])
