@@ -193,6 +193,57 @@ stf_status stf_lookup_accumulate(stf_texture tex, const stf_lookup_params* param
                                  int32_t n_samples, double* d_sum, double* d_sumsq,
                                  void* stream);
 
+/* ---------------------------------------------------------------- anisotropic filtering
+ *
+ * 2D textures only.  d_grad holds, per query, the texture-coordinate derivatives
+ * along the two screen axes (du/dx, dv/dx, du/dy, dv/dy) in uv units, float32,
+ * 16-byte aligned.  In level-0 texels the footprint's axes are (du/dx W, dv/dx H) and
+ * (du/dy W, dv/dy H); the longer is the major axis.  If the major axis is more than
+ * max_anisotropy times the minor one, the minor axis is lengthened to
+ * major / max_anisotropy (Section 5.2: the ratio is limited, 64 in the paper; pbrt
+ * uses 8); lod = log2(minor length).  1 <= max_anisotropy <= STF_EWA_MAX_ANISOTROPY.
+ * Derivatives that are not finite, or whose squared lengths in texels overflow
+ * float32, give a NaN lod (stf_anisotropic_lod) or the background 0 with tap level -1
+ * (the EWA lookups).  Every float32 step of the level and tap decisions is rounded
+ * individually in a fixed order, so the choices are reproducible by any float32
+ * implementation of the same steps. */
+#define STF_EWA_MAX_ANISOTROPY 64.0f
+
+/* Level of detail of each query's footprint (the anisotropic LOD of Section 5.2 and
+ * Appendix B), clamped to [0, levels - 1]; d_lod (n floats, caller-owned) can be passed
+ * to stf_lookup_batch, whose stochastic level choice floor(lod + u) is the listing's
+ * jitter by u - 1/2 followed by rounding. */
+stf_status stf_anisotropic_lod(stf_texture tex, const float* d_grad, int64_t n,
+                               float max_anisotropy, float* d_lod, void* stream);
+
+/* Elliptically weighted average (EWA; Section 5.3 and Appendix B, pbrt's filter).
+ * The level is chosen from the footprint's lod as params->level_mode says (stochastic:
+ * floor(lod + u) with word 3 of the query's Philox stream 0; nearest: floor(lod + 1/2)).
+ * At level L (W_L x H_L texels) the axes are scaled to that level's texels (a minor
+ * axis longer than 2 texels, possible only above the coarsest level, shrinks both
+ * axes so that it is 2) and the filter is the Gaussian table
+ * w = LUT[min(floor(Q * 128), 127)], LUT[i] = exp(-2 i/127) - exp(-2), over the
+ * ellipse Q(s, t) = A s^2 + B s t + C t^2 < 1 centred on (u W_L - 1/2, v H_L - 1/2),
+ * where (A, B, C) / F is the inverse of d0 d0^T + d1 d1^T + I; taps are clamped to the
+ * edge.  stf_lookup_batch_ewa returns one texel of the ellipse's bounding box drawn
+ * with probability w / sum(w): the smallest k, in row-major order (t, then s,
+ * ascending), with u S < C_k (u = word 0 of stream 0).  d_taps (nullable) receives
+ * (s, t, 0, L) of the drawn texel.  The deterministic form returns sum(w t) / sum(w)
+ * at one level (nearest) or two levels blended by frac(lod) (stochastic level mode),
+ * as pbrt does.  params->filter, reuse_xi and filter_width are ignored; bin_queries
+ * is STF_ERR_UNSUPPORTED.  d_uv: n x 2 floats (8-byte aligned); d_out: n x channels
+ * floats. */
+stf_status stf_lookup_batch_ewa(stf_texture tex, const stf_lookup_params* params,
+                                const float* d_uv, const float* d_grad, int64_t n,
+                                float max_anisotropy, float* d_out, int32_t* d_taps,
+                                void* stream);
+stf_status stf_lookup_batch_ewa_deterministic(stf_texture tex, const stf_lookup_params* params,
+                                              const float* d_uv, const float* d_grad, int64_t n,
+                                              float max_anisotropy, float* d_out, void* stream);
+
+/* The 128 float32 entries of the EWA weight table the library uses (host memory). */
+stf_status stf_ewa_weight_table(float* h_out);
+
 /* ---------------------------------------------------------------- neural textures
  *
  * A neural texture stores, for MIP levels 0 .. latent_levels-1, one latent texel

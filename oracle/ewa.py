@@ -65,6 +65,11 @@ def _dot(ax, ay, bx, by):
 def footprint(W, H, grad, max_anisotropy):
     """Per query: (major uv vector, minor uv vector after the anisotropy clamp, lod),
     float32.  grad: (N, 4) du/dx, dv/dx, du/dy, dv/dy in uv units."""
+    with np.errstate(over="ignore", invalid="ignore"):
+        return _footprint(W, H, grad, max_anisotropy)
+
+
+def _footprint(W, H, grad, max_anisotropy):
     g = _f(grad)
     Wf, Hf = F32(W), F32(H)
     ax, ay = _f(g[:, 0]), _f(g[:, 1])         # d_x in uv

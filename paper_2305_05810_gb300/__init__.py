@@ -19,7 +19,8 @@ __all__ = [
     "FILTER_LINEAR", "FILTER_BSPLINE3", "FILTER_CATMULL_ROM", "LEVEL_NEAREST",
     "LEVEL_STOCHASTIC", "library_path", "load", "NeuralDesc", "TrainConfig",
     "stf_create_neural_texture", "stf_neural_gradients", "stf_neural_train", "stf_neural_read",
-    "NeuralTexture", "KIND_NEURAL2D",
+    "NeuralTexture", "KIND_NEURAL2D", "stf_anisotropic_lod", "stf_lookup_batch_ewa",
+    "stf_lookup_batch_ewa_deterministic", "stf_ewa_weight_table", "STF_EWA_MAX_ANISOTROPY",
 ]
 
 KIND_TEX2D, KIND_DENSE3D, KIND_SPARSE3D, KIND_NEURAL2D = 0, 1, 2, 3
@@ -34,6 +35,7 @@ FILTERS = {"linear": FILTER_LINEAR, "bspline3": FILTER_BSPLINE3, "catmull_rom": 
            "fis_gaussian": FILTER_FIS_GAUSSIAN}
 LEVEL_NEAREST, LEVEL_STOCHASTIC = 0, 1
 STF_NOALLOC_MAX_QUERIES = 1 << 20   # include/stf.h
+STF_EWA_MAX_ANISOTROPY = 64.0       # include/stf.h
 
 STATUS = {0: "STF_OK", 1: "STF_ERR_INVALID_ARGUMENT", 2: "STF_ERR_INVALID_HANDLE",
           3: "STF_ERR_OUT_OF_MEMORY", 4: "STF_ERR_UNSUPPORTED", 5: "STF_ERR_CUDA",
@@ -110,12 +112,18 @@ def load(build_if_missing=True):
     lib.stf_neural_gradients.argtypes = [VP, VP, I64, VP, VP, VP, VP, VP]
     lib.stf_neural_train.argtypes = [VP, VP, P(TrainConfig), I32, VP, VP]
     lib.stf_neural_read.argtypes = [VP, VP, VP, VP]
+    F32 = ctypes.c_float
+    lib.stf_anisotropic_lod.argtypes = [VP, VP, I64, F32, VP, VP]
+    lib.stf_lookup_batch_ewa.argtypes = [VP, P(LookupParams), VP, VP, I64, F32, VP, VP, VP]
+    lib.stf_lookup_batch_ewa_deterministic.argtypes = [VP, P(LookupParams), VP, VP, I64, F32, VP, VP]
+    lib.stf_ewa_weight_table.argtypes = [VP]
     lib.stf_debug_fail_allocation.argtypes = [I64]
     lib.stf_debug_fail_allocation.restype = None
     for f in ("stf_create_texture", "stf_destroy", "stf_lookup_batch",
               "stf_lookup_batch_deterministic", "stf_lookup_accumulate", "stf_texture_bytes",
               "stf_synchronize", "stf_lookup_batch_binned_noalloc", "stf_create_neural_texture",
-              "stf_neural_gradients", "stf_neural_train", "stf_neural_read"):
+              "stf_neural_gradients", "stf_neural_train", "stf_neural_read", "stf_anisotropic_lod",
+              "stf_lookup_batch_ewa", "stf_lookup_batch_ewa_deterministic", "stf_ewa_weight_table"):
         getattr(lib, f).restype = I32
     _lib = lib
     return lib
@@ -205,6 +213,28 @@ def stf_lookup_accumulate(tex, params, coords, lod, n, n_samples, d_sum, d_sumsq
                                         _stream(stream)))
 
 
+def stf_anisotropic_lod(tex, grad, n, max_anisotropy, lod, stream=None):
+    _check(load().stf_anisotropic_lod(tex, _ptr(grad), int(n), float(max_anisotropy), _ptr(lod),
+                                      _stream(stream)))
+
+
+def stf_lookup_batch_ewa(tex, params, uv, grad, n, max_anisotropy, out, taps=None, stream=None):
+    _check(load().stf_lookup_batch_ewa(tex, ctypes.byref(params), _ptr(uv), _ptr(grad), int(n),
+                                       float(max_anisotropy), _ptr(out), _ptr(taps), _stream(stream)))
+
+
+def stf_lookup_batch_ewa_deterministic(tex, params, uv, grad, n, max_anisotropy, out, stream=None):
+    _check(load().stf_lookup_batch_ewa_deterministic(tex, ctypes.byref(params), _ptr(uv), _ptr(grad),
+                                                     int(n), float(max_anisotropy), _ptr(out),
+                                                     _stream(stream)))
+
+
+def stf_ewa_weight_table():
+    buf = (ctypes.c_float * 128)()
+    _check(load().stf_ewa_weight_table(ctypes.addressof(buf)))
+    return list(buf)
+
+
 def stf_texture_bytes(tex):
     b = ctypes.c_int64()
     _check(load().stf_texture_bytes(tex, ctypes.byref(b)))
@@ -285,6 +315,35 @@ class Texture:
         stf_lookup_accumulate(self.handle, make_params(**params), coords, lod, n, n_samples, s, s2,
                               stream)
         return s, s2
+
+
+    def lookup_ewa(self, uv, grad, max_anisotropy=STF_EWA_MAX_ANISOTROPY, *, out=None, taps=None,
+                   stream=None, **params):
+        import torch
+        n = uv.shape[0]
+        if out is None:
+            out = torch.empty((n, self.channels), dtype=torch.float32, device=uv.device)
+        stf_lookup_batch_ewa(self.handle, make_params(**params), uv, grad, n, max_anisotropy, out,
+                             taps, stream)
+        return out
+
+    def lookup_ewa_deterministic(self, uv, grad, max_anisotropy=STF_EWA_MAX_ANISOTROPY, *, out=None,
+                                 stream=None, **params):
+        import torch
+        n = uv.shape[0]
+        if out is None:
+            out = torch.empty((n, self.channels), dtype=torch.float32, device=uv.device)
+        stf_lookup_batch_ewa_deterministic(self.handle, make_params(**params), uv, grad, n,
+                                           max_anisotropy, out, stream)
+        return out
+
+    def anisotropic_lod(self, grad, max_anisotropy=STF_EWA_MAX_ANISOTROPY, *, out=None, stream=None):
+        import torch
+        n = grad.shape[0]
+        if out is None:
+            out = torch.empty((n,), dtype=torch.float32, device=grad.device)
+        stf_anisotropic_lod(self.handle, grad, n, max_anisotropy, out, stream)
+        return out
 
 
 class NeuralTexture(Texture):

@@ -13,6 +13,7 @@ bool handle_ok(stf_texture t);
 stf_status dispatch(Op op, stf_texture t, int filter, const LookupArgs& a, cudaStream_t s);
 stf_status check_lookup(stf_texture t, const stf_lookup_params* p, const float* coords,
                         const float* lod, int64_t n, const void* out);
+Tex2DView view2d(const stf_texture_s* t);
 LookupArgs make_args(const stf_lookup_params* p, const float* coords, const float* lod, int64_t n,
                      float* out, int32_t* taps);
 

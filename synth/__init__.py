@@ -185,3 +185,41 @@ def neural_init(size, latent_levels, seed=5, latent_scale=0.5):
         else:
             parts.append(np.zeros(shape[0]))
     return latents, np.concatenate(parts).astype(np.float32)
+
+
+def plane_view(W=1920, H=1080, seed=7, fov_deg=60.0, height=0.04, pitch_deg=12.0):
+    """Texture coordinates and their screen-space derivatives for a camera looking
+    across a textured ground plane (the textured square [0, 1]^2 of z = 0, uv = (x, y)),
+    the grazing view where footprints are long ellipses (Section 5.2's anisotropic
+    test scene is a textured plane).  The camera stands at a seeded point near the
+    y = 0 edge, `height` above the plane, yawed by a seeded angle, pitched down by
+    `pitch_deg`.  Per pixel whose ray hits the square: uv of the hit point and
+    (du/dx, dv/dx, du/dy, dv/dy), the differences to the hits of the rays through the
+    neighbouring pixels (+1 in x, +1 in y).  Returns (uv (n, 2), grad (n, 4)) float32."""
+    rng = np.random.default_rng(seed)
+    eye = np.array([rng.uniform(0.35, 0.65), rng.uniform(-0.05, 0.05), height])
+    yaw = np.radians(rng.uniform(-20.0, 20.0))
+    pitch = np.radians(-pitch_deg)
+    fwd = np.array([np.sin(yaw) * np.cos(pitch), np.cos(yaw) * np.cos(pitch), np.sin(pitch)])
+    right = np.array([np.cos(yaw), -np.sin(yaw), 0.0])
+    up = np.cross(right, fwd)
+    t = np.tan(np.radians(fov_deg) / 2)
+
+    def hits(px, py):
+        sx = (2 * (px + 0.5) / W - 1) * t * W / H
+        sy = (1 - 2 * (py + 0.5) / H) * t
+        d = fwd[None] + sx[:, None] * right[None] + sy[:, None] * up[None]
+        with np.errstate(divide="ignore", invalid="ignore"):
+            s = -eye[2] / d[:, 2]
+        p = eye[None] + s[:, None] * d
+        return p[:, :2], s
+
+    py, px = np.mgrid[0:H, 0:W]
+    px, py = px.ravel().astype(np.float64), py.ravel().astype(np.float64)
+    p, s = hits(px, py)
+    px1, s1 = hits(px + 1, py)
+    py1, s2 = hits(px, py + 1)
+    ok = (s > 0) & (s1 > 0) & (s2 > 0) & np.all((p >= 0) & (p < 1), axis=1)
+    uv = p[ok]
+    grad = np.concatenate([px1[ok] - uv, py1[ok] - uv], axis=1)
+    return uv.astype(np.float32), grad.astype(np.float32)

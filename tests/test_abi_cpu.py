@@ -66,6 +66,17 @@ def test_argument_errors_without_gpu(lib):
     with pytest.raises(stf.StfError) as e:
         stf.stf_destroy(0x1234)
     assert e.value.status == 2
+    assert lib.stf_anisotropic_lod(bogus, None, 0, ctypes.c_float(8.0), None, None) == 2
+    assert lib.stf_lookup_batch_ewa(bogus, ctypes.byref(p), None, None, 0, ctypes.c_float(8.0),
+                                    None, None, None) == 2
+
+
+def test_ewa_weight_table_is_the_oracle_table(lib):
+    """The library's EWA weight table (a host-side table, no GPU involved) holds the
+    same float32 values as the oracle's: exp(-2 r) - exp(-2) at r = i / 127."""
+    import numpy as np
+    from oracle import ewa
+    assert np.array_equal(np.array(stf.stf_ewa_weight_table(), dtype=np.float32), ewa.weight_lut())
 
 
 def test_binding_raises_when_library_missing(monkeypatch, tmp_path):

@@ -1,0 +1,174 @@
+"""GPU parity for the anisotropic level of detail and EWA lookups (Sections 5.2, 5.3;
+Appendix B) through the C ABI against the float32-decision / float64-value oracle
+(`oracle/ewa.py`).
+
+Bar: every step of the EWA tap decision is an individually rounded float32
+operation in the same order on both sides, so the drawn texel must match bit for
+bit.  The one exception is the level: log2 of the minor axis may differ by an ulp
+between CUDA's log2f and numpy's, so a level choice within 4e-6 of a level boundary
+is exempt (oracle-reported).  Stochastic values are stored texels (exact; levels
+above 0 agree to the float32 rounding of the library's box pyramid, 2e-6 relative).
+Deterministic values: float32 sums of n positive weights and weighted texels, so
+|gpu - ref| <= 2e-6 |ref| + 4 n 2^-24 max|t| per level."""
+import numpy as np
+import pytest
+import torch
+
+import paper_2305_05810_gb300 as stf
+import synth
+from oracle import ewa, textures
+from parity import dev, to_dev
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    stf.load()
+
+
+def _queries(n, size, seed):
+    """Plane-view footprints (scaled to a size^2 texture) plus random and edge cases."""
+    uv, g = synth.plane_view(W=320, H=180, seed=seed)
+    pick = np.random.default_rng(seed).choice(uv.shape[0], min(n, uv.shape[0]), replace=False)
+    uv, g = uv[pick], g[pick]
+    rng = np.random.default_rng(seed + 1)
+    m = 400
+    ru = rng.uniform(-0.1, 1.1, (m, 2)).astype(np.float32)
+    rg = (rng.standard_normal((m, 4)) * np.exp(rng.uniform(-3, 4, (m, 1))) / size).astype(np.float32)
+    edge_uv = np.array([[np.nan, 0.5], [0.5, 0.5], [0.5, 0.5], [0.5, 0.5], [0.5, 0.5],
+                        [0.25, 0.75], [1e30, -1e30], [0.5, 0.5]], dtype=np.float32)
+    edge_g = np.array([[1e-3, 0, 0, 1e-3], [np.inf, 0, 0, 1e-3], [0, 0, 0, 0], [1e20, 0, 0, 1e-3],
+                       [1.0, 0.0, 0.0, 1e-6], [0, 5.0, 3.0, 0], [1e-3, 0, 0, 1e-3],
+                       [1e-5, 1e-5, -1e-5, 1e-5]], dtype=np.float32)
+    return (np.concatenate([uv, ru, edge_uv]).astype(np.float32),
+            np.ascontiguousarray(np.concatenate([g, rg, edge_g]).astype(np.float32)))
+
+
+def _texture(size=64, C=4, levels=7, seed=21):
+    base = synth.texture2d(size, size, C, seed=seed)
+    T = stf.Texture(stf.KIND_TEX2D, base, dims=(size, size, 1), channels=C, mip_levels=levels,
+                    generate_mips=True)
+    ref = textures.Texture2D.box_pyramid(base.astype(np.float64), levels)
+    return T, ref
+
+
+def test_anisotropic_lod_matches_oracle():
+    T, ref = _texture()
+    uv, g = _queries(3000, 64, 5)
+    for ma in (1.0, 8.0, 64.0):
+        lod = T.anisotropic_lod(to_dev(g), ma).cpu().numpy()
+        _, _, r = ewa.footprint(64, 64, g, ma)
+        fin = ewa.footprint_finite(64, 64, g)
+        r = np.clip(r, 0, 6)
+        assert np.all(np.isnan(lod[~fin]))
+        d = np.abs(lod[fin].astype(np.float64) - r[fin])
+        assert np.all(d <= 2.5e-7 * np.maximum(np.abs(r[fin]), 1.0)), np.max(d)
+
+
+@pytest.mark.parametrize("level_mode", [stf.LEVEL_NEAREST, stf.LEVEL_STOCHASTIC])
+@pytest.mark.parametrize("max_aniso", [8.0, 64.0])
+def test_ewa_stochastic_matches_oracle(level_mode, max_aniso):
+    T, ref = _texture()
+    uv, g = _queries(2500, 64, 6)
+    n = uv.shape[0]
+    taps = torch.empty((n, 4), dtype=torch.int32, device=dev())
+    out = T.lookup_ewa(to_dev(uv), to_dev(g), max_aniso, taps=taps, seed=17, sample_index=4,
+                       level_mode=level_mode)
+    rv, rt, ex = ewa.lookup(ref, uv, g, max_aniso, stochastic_form=True, level_mode=level_mode,
+                            seed=17, sample_index=4)
+    torch.cuda.synchronize()
+    gt = taps.cpu().numpy().astype(np.int64)
+    same = np.all(gt == rt, axis=1)
+    bad = ~same & ~ex
+    assert not np.any(bad), "tap mismatch at %s: gpu %s ref %s" % (
+        np.nonzero(bad)[0][:5], gt[bad][:5], rt[bad][:5])
+    assert np.sum(ex) <= n // 200
+    gv = out.cpu().numpy().astype(np.float64)
+    assert np.all(np.abs(gv - rv)[same] <= 2e-6 * np.abs(rv[same]))
+    stf.stf_synchronize(T.handle)
+
+
+def _ntaps(ref, uv, g, ma, level_mode):
+    """Weighted texels per query at each level the deterministic filter visits."""
+    W0, H0 = ref.size(0)
+    major, minor, lod = ewa.footprint(W0, H0, g, ma)
+    out = np.zeros(uv.shape[0])
+    for q in range(uv.shape[0]):
+        if not (np.all(np.isfinite(uv[q])) and ewa.footprint_finite(W0, H0, g[q:q + 1])[0]):
+            continue
+        L0, L1, frac, _ = ewa._levels(lod[q], len(ref.levels), level_mode, 0.0, False)
+        for L in ({L0, L1} if frac > 0 else {L0}):
+            WL, HL = ref.size(L)
+            st = ewa.raster(uv[q], WL, HL)
+            ax = ewa.level_axes(ref, L, (major[0][q:q + 1], major[1][q:q + 1]), (minor[0][q:q + 1], minor[1][q:q + 1]))
+            A, B, C, hs, ht = ewa.ellipse(*[a[0] for a in ax])
+            out[q] = max(out[q], len(ewa.texels_and_weights(st[0], st[1], A, B, C, hs, ht)[2]))
+    return out
+
+
+@pytest.mark.parametrize("level_mode", [stf.LEVEL_NEAREST, stf.LEVEL_STOCHASTIC])
+def test_ewa_deterministic_matches_oracle(level_mode):
+    T, ref = _texture(C=2)
+    uv, g = _queries(1500, 64, 8)
+    ma = 16.0
+    out = T.lookup_ewa_deterministic(to_dev(uv), to_dev(g), ma, level_mode=level_mode)
+    rv, _, _ = ewa.lookup(ref, uv, g, ma, stochastic_form=False, level_mode=level_mode)
+    ntap = _ntaps(ref, uv, g, ma, level_mode)
+    err = np.abs(out.cpu().numpy().astype(np.float64) - rv)
+    lim = 2e-6 * np.abs(rv) + (4 * 2 * ntap * 2.0 ** -24)[:, None]
+    assert np.all(err <= lim), np.max(err / lim)
+
+
+def test_ewa_unbiased_over_samples():
+    """Mean of 1024 stochastic EWA lookups per query (stochastic level, texel) against
+    the deterministic EWA blended over the two levels around lod; the variance is the
+    sample variance (z-test, 1% tail allowance)."""
+    T, ref = _texture(C=1, seed=23)
+    uv, g = _queries(2000, 64, 9)
+    ok = np.all(np.isfinite(uv), axis=1) & ewa.footprint_finite(64, 64, g)
+    uv, g = uv[ok], g[ok]
+    d_uv, d_g = to_dev(uv), to_dev(g)
+    S = 1024
+    acc = torch.zeros((uv.shape[0], 1), dtype=torch.float64, device=dev())
+    acc2 = torch.zeros_like(acc)
+    out = torch.empty((uv.shape[0], 1), dtype=torch.float32, device=dev())
+    for s in range(S):
+        T.lookup_ewa(d_uv, d_g, 16.0, out=out, seed=5, sample_index=s)
+        o = out.double()
+        acc += o
+        acc2 += o * o
+    mean = (acc / S).cpu().numpy()
+    var = np.maximum((acc2 / S).cpu().numpy() - mean ** 2, 1e-12)
+    rv, _, _ = ewa.lookup(ref, uv, g, 16.0, stochastic_form=False)
+    z = (mean - rv) / np.sqrt(var / S)
+    assert np.mean(np.abs(z) > 3.5) <= 0.01
+    assert abs(np.sum(mean - rv) / np.sqrt(np.sum(var) / S)) < 4
+
+
+def test_ewa_argument_checks():
+    T, _ = _texture(size=16, levels=5)
+    uv = to_dev(np.full((4, 2), 0.5, dtype=np.float32))
+    g = to_dev(np.full((4, 4), 0.01, dtype=np.float32))
+    out = torch.empty((4, 4), device=dev())
+    p = stf.make_params()
+    for ma in (0.5, 65.0, float("nan")):
+        with pytest.raises(stf.StfError) as e:
+            stf.stf_lookup_batch_ewa(T.handle, p, uv, g, 4, ma, out)
+        assert e.value.status == 1
+    with pytest.raises(stf.StfError) as e:
+        stf.stf_lookup_batch_ewa(T.handle, stf.make_params(bin_queries=True), uv, g, 4, 8.0, out)
+    assert e.value.status == 4
+    gflat = torch.zeros(20, device=dev())
+    with pytest.raises(stf.StfError) as e:       # 4-byte offset: not 16-byte aligned
+        stf.stf_lookup_batch_ewa(T.handle, p, uv, gflat[1:], 4, 8.0, out)
+    assert e.value.status == 1
+    vals = synth.dense_density(n=8, seed=2, period=4.0)
+    D = stf.Texture(stf.KIND_DENSE3D, vals, dims=(8, 8, 8))
+    with pytest.raises(stf.StfError) as e:
+        stf.stf_lookup_batch_ewa(D.handle, p, uv, g, 4, 8.0, out)
+    assert e.value.status == 4
+    stf.stf_lookup_batch_ewa(T.handle, p, uv, g, 0, 8.0, out)      # n = 0: no-op
+    torch.cuda.synchronize()
