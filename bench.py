@@ -52,7 +52,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="dense",
-                    choices=["dense", "tex2d", "sparse", "sparse_e4m3", "neural", "serving", "aniso"])
+                    choices=["dense", "tex2d", "sparse", "sparse_e4m3", "neural", "serving", "aniso",
+                             "dct"])
     ap.add_argument("--requests", type=int, default=600, help="serving: number of requests")
     ap.add_argument("--train-steps", type=int, default=400)
     ap.add_argument("--filter", default=None, choices=["linear", "bspline3", "catmull_rom"],
@@ -223,15 +224,17 @@ def pct(xs, p):
     return xs[i]
 
 
-KERNEL_SOURCES = {"dense": "stf_grid.cu", "tex2d": "stf_grid.cu", "sparse": "stf_sparse.cu",
-                  "sparse_e4m3": "stf_sparse.cu", "neural": "stf_neural.cu"}
+KERNEL_SOURCES = {"dense": ("stf_grid.cu",), "tex2d": ("stf_tex2d.cuh", "stf_tex2d_f32.cu"),
+                  "sparse": ("stf_sparse.cu",), "sparse_e4m3": ("stf_sparse.cu",),
+                  "neural": ("stf_neural.cu",), "aniso": ("stf_ewa.cu",),
+                  "dct": ("stf_tex2d.cuh", "stf_tex2d_dct.cu")}
 
 
 def kernel_hash(workload):
     """Hash of the sources that build the workload's lookup kernel."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2305_05810_gb300", "csrc")
-    for f in ("stf_device.cuh", "stf_types.h", "stf_launch.h", KERNEL_SOURCES[workload]):
+    for f in ("stf_device.cuh", "stf_types.h", "stf_launch.h") + KERNEL_SOURCES[workload]:
         h.update(open(os.path.join(csrc, f), "rb").read())
     return h.hexdigest()[:16]
 
@@ -387,7 +390,7 @@ def run_serving(args):
 
 
 def run_aniso(args):
-    """Anisotropic minification (Sections 5.2, 5.3): a 1024^2 RGBA FP16 texture with its
+    """Anisotropic minification (Sections 4.2, 5.2): a 1024^2 RGBA FP16 texture with its
     full box pyramid (11 levels) seen across a ground plane at 3840x2160 (one query per
     pixel that hits the textured square, with its screen-space uv derivatives).  The
     timed step is the stochastic EWA lookup (max anisotropy 16, stochastic level, one
@@ -468,8 +471,8 @@ def run_aniso(args):
                                "%d queries with uv derivatives, EWA max anisotropy 16" % n,
                    "l2": "inputs and outputs larger than L2"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                     "frac": achieved / hbm, "traffic": None, "algorithmic_bytes_per_lookup": algo,
-                     "peak_source": peak_kind,
+                     "frac": achieved / hbm, "traffic": ncu_traffic("aniso", "ewa"),
+                     "algorithmic_bytes_per_lookup": algo, "peak_source": peak_kind,
                      "note": "the kernel is bound by the per-texel ellipse arithmetic, not by bytes"},
         "e2e": {"value": n * len(pe) / (te / 1000.0), "unit": "lookups/s",
                 "h2d_bytes_per_step": n * 24, "d2h_bytes_per_step": n * 16},
@@ -484,6 +487,106 @@ def run_aniso(args):
         dt = time.perf_counter() - t0
         line["cpu_baseline"] = {"value": m / dt, "unit": "lookups/s", "cores": 1, "kind": "oracle",
                                 "sample": "first %d queries, stochastic EWA" % m}
+    print(json.dumps(line), flush=True)
+    tex.close()
+    return 0
+
+
+def run_dct(args):
+    """DCT-compressed texture set (Section 5.2, "Texture compression"): a 4096^2
+    8-channel texture set (value noise in [0, 1]), full box pyramid (13 levels),
+    encoded to six DCT coefficients per 8x8 block and channel (32 bits: 16x smaller
+    than 8-bit texels), seen across a ground plane at 3840x2160 (one query per pixel that
+    hits the plane; level of detail from the anisotropic LOD of the footprint, computed
+    once before timing).  The timed step is stochastic trilinear filtering (stochastic
+    level, one bilinear tap: one decoded texel); extras: deterministic trilinear (eight
+    decoded texels), the same pair on the uncompressed FP16 texture, and stochastic /
+    deterministic triplanar mapping of a sphere (one vs 24 decoded texels)."""
+    import torch
+    import paper_2305_05810_gb300 as stf
+    import synth
+    stf.load()
+    dev = torch.device("cuda", torch.cuda.current_device())
+    size, C, levels = 4096, 8, 13
+    base = synth.texture2d(size, size, C, seed=1)
+    tex = stf.Texture(stf.KIND_TEX2D, base, dims=(size, size, 1), channels=C, mip_levels=levels,
+                      generate_mips=True, fmt=stf.FMT_DCT6)
+    uv_h, g_h = synth.plane_view(W=3840, H=2160, seed=7)
+    n = uv_h.shape[0]
+    uv, g = torch.from_numpy(uv_h).to(dev), torch.from_numpy(g_h).to(dev)
+    lod = tex.anisotropic_lod(g, 16.0)
+    out = torch.empty((n, C), dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+    ps, pd = stf.make_params("linear", seed=2024), stf.make_params("linear")
+
+    def sto():
+        stf.stf_lookup_batch(tex.handle, ps, uv, lod, n, out, None, stream)
+
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        per, total, win = time_steps(torch, sto, args.steps, args.warmup, stream, return_window=True)
+        clk.mark(*win)
+    stf.stf_synchronize(tex.handle, stream)
+    value = n * args.steps / (total / 1000.0)
+    extras = {}
+    if not args.quick:
+        f16 = stf.Texture(stf.KIND_TEX2D, base, dims=(size, size, 1), channels=C, mip_levels=levels,
+                          generate_mips=True, fmt=stf.FMT_F16)
+        pts, nrm = synth.sphere_points(3840 * 2160, seed=8)
+        m = pts.shape[0]
+        dp, dn = torch.from_numpy(pts).to(dev), torch.from_numpy(nrm).to(dev)
+        tlod = torch.from_numpy(synth.lods(m, seed=9, lo=0.0, hi=4.0)).to(dev)
+        tout = torch.empty((m, C), dtype=torch.float32, device=dev)
+        variants = [
+            ("deterministic_trilinear", n, lambda: stf.stf_lookup_batch_deterministic(
+                tex.handle, pd, uv, lod, n, out, stream)),
+            ("fp16_uncompressed_stochastic_trilinear", n, lambda: stf.stf_lookup_batch(
+                f16.handle, ps, uv, lod, n, out, None, stream)),
+            ("fp16_uncompressed_deterministic_trilinear", n, lambda: stf.stf_lookup_batch_deterministic(
+                f16.handle, pd, uv, lod, n, out, stream)),
+            ("triplanar_stochastic_trilinear", m, lambda: stf.stf_lookup_batch_triplanar(
+                tex.handle, ps, dp, dn, tlod, m, 1.0, tout, None, stream)),
+            ("triplanar_deterministic_trilinear", m, lambda: stf.stf_lookup_batch_triplanar_deterministic(
+                tex.handle, pd, dp, dn, tlod, m, 1.0, tout, stream)),
+        ]
+        for name, cnt, fn in variants:
+            p2, t2 = time_steps(torch, fn, max(3, args.steps // 2), 2, stream)
+            extras[name] = {"lookups_per_s": cnt * len(p2) / (t2 / 1000.0), "ms_p50": pct(p2, 50),
+                            "ms_p99": pct(p2, 99)}
+        extras["speedup_vs_deterministic"] = value / extras["deterministic_trilinear"]["lookups_per_s"]
+        extras["triplanar_speedup"] = (extras["triplanar_stochastic_trilinear"]["lookups_per_s"] /
+                                       extras["triplanar_deterministic_trilinear"]["lookups_per_s"])
+        extras["texture_bytes"] = {"dct6": tex.nbytes, "fp16": f16.nbytes}
+        f16.close()
+    h_uv = torch.from_numpy(uv_h).pin_memory()
+    h_lod = lod.cpu().pin_memory()
+    h_out = torch.empty((n, C), dtype=torch.float32).pin_memory()
+    d_uv, d_lod = torch.empty_like(uv), torch.empty_like(lod)
+
+    def e2e_step():
+        d_uv.copy_(h_uv, non_blocking=True)
+        d_lod.copy_(h_lod, non_blocking=True)
+        stf.stf_lookup_batch(tex.handle, ps, d_uv, d_lod, n, out, None, stream)
+        h_out.copy_(out, non_blocking=True)
+
+    pe, te = time_steps(torch, e2e_step, max(3, args.steps // 2), 2, stream)
+    hbm, peak_kind = peaks()
+    algo = 8 + 4 + 4 * C + 4 * C
+    achieved = algo * n / (statistics.mean(per) / 1000.0) / 1e9
+    line = {
+        "metric": "DCT-texture lookups/s (stochastic trilinear)", "value": value, "unit": "lookups/s",
+        "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": total / args.steps,
+        "ms_p50": pct(per, 50), "ms_p99": pct(per, 99), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32 (DCT6 texels)", "data": "synthetic",
+        "config": {"workload": "dct: 4096^2 x 8 channels DCT6 (6 coefficients per 8x8 block, 7/5-bit "
+                               "codes) + 13 levels, ground plane at 3840x2160, %d queries, anisotropic "
+                               "LOD" % n, "l2": "inputs and outputs larger than L2"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                     "frac": achieved / hbm, "traffic": ncu_traffic("dct", "linear"),
+                     "algorithmic_bytes_per_lookup": algo, "peak_source": peak_kind},
+        "e2e": {"value": n * len(pe) / (te / 1000.0), "unit": "lookups/s",
+                "h2d_bytes_per_step": n * 12, "d2h_bytes_per_step": n * 4 * C},
+        "gpu_launches": args.warmup + args.steps, "clocks": clk.summary(), "extras": extras,
+    }
     print(json.dumps(line), flush=True)
     tex.close()
     return 0
@@ -710,6 +813,8 @@ def main():
         return run_serving(args)
     if args.workload == "aniso":
         return run_aniso(args)
+    if args.workload == "dct":
+        return run_dct(args)
     return run_ours(args)
 
 

@@ -68,8 +68,21 @@ typedef enum {
 typedef enum {
   STF_FMT_F32 = 0,        /* IEEE binary32 texels */
   STF_FMT_F16 = 1,        /* IEEE binary16 texels (round-to-nearest-even at create) */
-  STF_FMT_E4M3_SCALED = 2 /* sparse only: OCP FP8 E4M3 codes with one float32 scale
+  STF_FMT_E4M3_SCALED = 2, /* sparse only: OCP FP8 E4M3 codes with one float32 scale
                              per leaf, scale = max|v| / 448 */
+  STF_FMT_DCT6 = 3        /* 2D only: DCT-compressed 8x8 blocks (Section 5.2, "Texture
+                             compression"), 32 bits per block and channel: the six
+                             coefficients (u, v) = (0,0), (1,0), (0,1), (2,0), (1,1), (0,2)
+                             of the orthonormal 8-point DCT-II (u along x), DC code
+                             round(DC 127 / 8) in [0, 127] (bits 0-6; texel values in
+                             [0, 1], DC = 8 x block mean), AC code j round(AC 15 / R_c)
+                             in [-15, 15] (bits 7+5j .. 11+5j, two's complement), R_c =
+                             largest |AC| of channel c over the whole pyramid (0 below
+                             2^-20), rounding half away from zero.  Each level is
+                             ceil(W_L/8) x ceil(H_L/8) blocks, edge texels repeated
+                             past the level's edge, and is encoded in float64 from the
+                             float32 level at creation.  Lookups decode the texels they
+                             fetch (one per stochastic lookup) in float32. */
 } stf_format;
 
 typedef enum {
@@ -83,7 +96,7 @@ typedef enum {
                                  W+ t(j+) - W- t(j-); two texel fetches, lower variance.
                                  The deterministic form equals STF_FILTER_CATMULL_ROM.
                                  reuse_xi is ignored.  Not offered for neural textures. */
-  /* Filter importance sampling (Section 3, "Filter Importance Sampling"): a
+  /* Filter importance sampling (Section 4.4, "Filter Importance Sampling"): a
    * continuous offset s is drawn from a density and the texel nearest to x + s,
    * floor(x + s + 1/2), is returned unscaled.  The nearest-texel step convolves the
    * density with a unit box, which gives the filter each entry names.  reuse_xi is
@@ -216,7 +229,7 @@ stf_status stf_lookup_accumulate(stf_texture tex, const stf_lookup_params* param
 stf_status stf_anisotropic_lod(stf_texture tex, const float* d_grad, int64_t n,
                                float max_anisotropy, float* d_lod, void* stream);
 
-/* Elliptically weighted average (EWA; Section 5.3 and Appendix B, pbrt's filter).
+/* Elliptically weighted average (EWA; Section 4.2 and Appendix B, pbrt's filter).
  * The level is chosen from the footprint's lod as params->level_mode says (stochastic:
  * floor(lod + u) with word 3 of the query's Philox stream 0; nearest: floor(lod + 1/2)).
  * At level L (W_L x H_L texels) the axes are scaled to that level's texels (a minor
@@ -243,6 +256,27 @@ stf_status stf_lookup_batch_ewa_deterministic(stf_texture tex, const stf_lookup_
 
 /* The 128 float32 entries of the EWA weight table the library uses (host memory). */
 stf_status stf_ewa_weight_table(float* h_out);
+
+/* Triplanar mapping (Section 5.2, "Triplanar mapping"; Eq. 3) over a 2D texture (plain
+ * or DCT6).  d_pos and d_normal: n x 3 floats each (4-byte aligned); the three planes
+ * YZ, XZ and XY look the texture up at uv = scale (p_y, p_z), scale (p_x, p_z),
+ * scale (p_x, p_y) with weights |n_x|, |n_y|, |n_z| / (|n_x| + |n_y| + |n_z|).  The
+ * stochastic form draws one plane with probability equal to its weight (the smallest
+ * k with u S < C_k over the planes in that order, float32, u = word 2 of the query's
+ * Philox stream 0) and filters that plane's lookup stochastically with
+ * params->filter (taps and level as stf_lookup_batch, words 0, 1 and 3); d_taps
+ * (nullable) receives (x, y, plane, level).  The deterministic form blends the three
+ * deterministic lookups.  d_lod (nullable) is one lod per query, used by every plane.
+ * A non-finite position or normal, or a zero normal, gives 0 and tap level -1.
+ * STF_FILTER_CATMULL_ROM_POSITIVIZED and bin_queries are STF_ERR_UNSUPPORTED. */
+stf_status stf_lookup_batch_triplanar(stf_texture tex, const stf_lookup_params* params,
+                                      const float* d_pos, const float* d_normal, const float* d_lod,
+                                      int64_t n, float scale, float* d_out, int32_t* d_taps,
+                                      void* stream);
+stf_status stf_lookup_batch_triplanar_deterministic(stf_texture tex, const stf_lookup_params* params,
+                                                    const float* d_pos, const float* d_normal,
+                                                    const float* d_lod, int64_t n, float scale,
+                                                    float* d_out, void* stream);
 
 /* ---------------------------------------------------------------- neural textures
  *

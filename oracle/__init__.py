@@ -13,10 +13,10 @@ Modules (each cites the passage of the paper it follows):
 * ``filters``  -- deterministic (Eq. 2, Eq. 9) and stochastic (Eq. 3, sampling
   arrays of Section 2.2) lookups, positivization, and the exact expectation by
   enumeration.
-* ``fis``      -- filter importance sampling (Section 3): B-splines by sums of
+* ``fis``      -- filter importance sampling (Section 4.4): B-splines by sums of
   uniforms, the Gaussian by Box-Muller, nearest-texel lookup.
 * ``ewa``      -- anisotropic level of detail and (stochastic) EWA filtering
-  (Sections 5.2, 5.3; Appendix B).
+  (Sections 4.2, 5.2; Appendix B).
 * ``dct``      -- DCT-compressed textures and stochastic triplanar mapping
   (Section 5.2).
 * ``mlp``      -- float64 forward and backward of the neural-texture decoder.

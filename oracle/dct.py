@@ -235,7 +235,7 @@ def lookup_triplanar(tex, p, n, scale, lod, filt, *, stochastic_form, level_mode
     uv = np.take_along_axis(np.stack(uvs), k[None, :, None].repeat(2, axis=2), axis=0)[0]
     val, taps, ex = filters.lookup_2d(tex, uv, lod, filt, stochastic_form=True, level_mode=level_mode,
                                       qid=qid, sample_index=sample_index, seed=seed, width=width)
-    taps[:, 2] = k
+    taps[:, 2] = np.where(taps[:, 3] >= 0, k, taps[:, 2])
     val[~finite] = 0.0
     taps[~finite] = (0, 0, 0, -1)
     return val, taps, (ex | ex_plane) & finite

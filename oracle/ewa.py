@@ -11,7 +11,7 @@ only).
   level around lod (stochastic: floor(lod + u); deterministic: blend of floor(lod)
   and the next level), as the other 2D lookups do.
 
-* EWA (Greene and Heckbert; Section 5.3 and the stochastic EWA listing of
+* EWA (Greene and Heckbert; Section 4.2 and the stochastic EWA listing of
   Appendix B, which samples pbrt's EWA filter).  At level L with axes d0, d1 in
   that level's texels, the filter is a Gaussian over the ellipse
   Q(s, t) = A s^2 + B s t + C t^2 < 1 around the lookup's raster position, where

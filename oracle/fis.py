@@ -1,6 +1,6 @@
 """Filter importance sampling, float64 (test infrastructure only).
 
-Section 3, "Filter Importance Sampling (FIS)": instead of drawing one of the
+Section 4.4, "Filter Importance Sampling (FIS)": instead of drawing one of the
 discrete taps, FIS draws a continuous offset s from the filter's own density and
 returns the texel nearest to x + s, the texel with index floor(x + s + 1/2) in
 raster coordinates (texel i centred at i).  Taking the nearest texel reconstructs

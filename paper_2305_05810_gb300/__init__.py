@@ -21,11 +21,12 @@ __all__ = [
     "stf_create_neural_texture", "stf_neural_gradients", "stf_neural_train", "stf_neural_read",
     "NeuralTexture", "KIND_NEURAL2D", "stf_anisotropic_lod", "stf_lookup_batch_ewa",
     "stf_lookup_batch_ewa_deterministic", "stf_ewa_weight_table", "STF_EWA_MAX_ANISOTROPY",
+    "stf_lookup_batch_triplanar", "stf_lookup_batch_triplanar_deterministic", "FMT_DCT6",
 ]
 
 KIND_TEX2D, KIND_DENSE3D, KIND_SPARSE3D, KIND_NEURAL2D = 0, 1, 2, 3
 NEURAL_LATENT, NEURAL_HIDDEN, NEURAL_OUT, NEURAL_PARAMS = 8, 64, 7, 5191
-FMT_F32, FMT_F16, FMT_E4M3_SCALED = 0, 1, 2
+FMT_F32, FMT_F16, FMT_E4M3_SCALED, FMT_DCT6 = 0, 1, 2, 3
 FILTER_LINEAR, FILTER_BSPLINE3, FILTER_CATMULL_ROM, FILTER_CATMULL_ROM_POSITIVIZED = 0, 1, 2, 3
 FILTER_FIS_LINEAR, FILTER_FIS_BSPLINE3, FILTER_FIS_GAUSSIAN = 4, 5, 6
 FIS_MAX_WIDTH = 8.0                  # include/stf.h STF_FIS_MAX_WIDTH
@@ -117,13 +118,17 @@ def load(build_if_missing=True):
     lib.stf_lookup_batch_ewa.argtypes = [VP, P(LookupParams), VP, VP, I64, F32, VP, VP, VP]
     lib.stf_lookup_batch_ewa_deterministic.argtypes = [VP, P(LookupParams), VP, VP, I64, F32, VP, VP]
     lib.stf_ewa_weight_table.argtypes = [VP]
+    lib.stf_lookup_batch_triplanar.argtypes = [VP, P(LookupParams), VP, VP, VP, I64, F32, VP, VP, VP]
+    lib.stf_lookup_batch_triplanar_deterministic.argtypes = [VP, P(LookupParams), VP, VP, VP, I64, F32,
+                                                             VP, VP]
     lib.stf_debug_fail_allocation.argtypes = [I64]
     lib.stf_debug_fail_allocation.restype = None
     for f in ("stf_create_texture", "stf_destroy", "stf_lookup_batch",
               "stf_lookup_batch_deterministic", "stf_lookup_accumulate", "stf_texture_bytes",
               "stf_synchronize", "stf_lookup_batch_binned_noalloc", "stf_create_neural_texture",
               "stf_neural_gradients", "stf_neural_train", "stf_neural_read", "stf_anisotropic_lod",
-              "stf_lookup_batch_ewa", "stf_lookup_batch_ewa_deterministic", "stf_ewa_weight_table"):
+              "stf_lookup_batch_ewa", "stf_lookup_batch_ewa_deterministic", "stf_ewa_weight_table",
+              "stf_lookup_batch_triplanar", "stf_lookup_batch_triplanar_deterministic"):
         getattr(lib, f).restype = I32
     _lib = lib
     return lib
@@ -227,6 +232,17 @@ def stf_lookup_batch_ewa_deterministic(tex, params, uv, grad, n, max_anisotropy,
     _check(load().stf_lookup_batch_ewa_deterministic(tex, ctypes.byref(params), _ptr(uv), _ptr(grad),
                                                      int(n), float(max_anisotropy), _ptr(out),
                                                      _stream(stream)))
+
+
+def stf_lookup_batch_triplanar(tex, params, pos, normal, lod, n, scale, out, taps=None, stream=None):
+    _check(load().stf_lookup_batch_triplanar(tex, ctypes.byref(params), _ptr(pos), _ptr(normal), _ptr(lod),
+                                             int(n), float(scale), _ptr(out), _ptr(taps), _stream(stream)))
+
+
+def stf_lookup_batch_triplanar_deterministic(tex, params, pos, normal, lod, n, scale, out, stream=None):
+    _check(load().stf_lookup_batch_triplanar_deterministic(tex, ctypes.byref(params), _ptr(pos),
+                                                           _ptr(normal), _ptr(lod), int(n), float(scale),
+                                                           _ptr(out), _stream(stream)))
 
 
 def stf_ewa_weight_table():
@@ -335,6 +351,26 @@ class Texture:
             out = torch.empty((n, self.channels), dtype=torch.float32, device=uv.device)
         stf_lookup_batch_ewa_deterministic(self.handle, make_params(**params), uv, grad, n,
                                            max_anisotropy, out, stream)
+        return out
+
+    def lookup_triplanar(self, pos, normal, scale=1.0, lod=None, *, out=None, taps=None, stream=None,
+                         **params):
+        import torch
+        n = pos.shape[0]
+        if out is None:
+            out = torch.empty((n, self.channels), dtype=torch.float32, device=pos.device)
+        stf_lookup_batch_triplanar(self.handle, make_params(**params), pos, normal, lod, n, scale, out,
+                                   taps, stream)
+        return out
+
+    def lookup_triplanar_deterministic(self, pos, normal, scale=1.0, lod=None, *, out=None, stream=None,
+                                       **params):
+        import torch
+        n = pos.shape[0]
+        if out is None:
+            out = torch.empty((n, self.channels), dtype=torch.float32, device=pos.device)
+        stf_lookup_batch_triplanar_deterministic(self.handle, make_params(**params), pos, normal, lod, n,
+                                                 scale, out, stream)
         return out
 
     def anisotropic_lod(self, grad, max_anisotropy=STF_EWA_MAX_ANISOTROPY, *, out=None, stream=None):

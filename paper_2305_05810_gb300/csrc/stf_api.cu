@@ -9,6 +9,8 @@
 #include <string>
 #include <unordered_set>
 
+#include <cmath>
+
 #include "stf_internal.h"
 
 namespace {
@@ -84,7 +86,63 @@ static void free_texture(stf_texture_s* t) {
 
 static int pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
 
+// DCT6 2D texture: the float32 pyramid is built as for the other formats, then each
+// level is encoded (float64) into 32-bit block codes.
+static stf_status create_dct(stf_texture_s* t, const stf_texture_desc* d, cudaStream_t s) {
+  const int C = t->channels;
+  int64_t texels = 0, words = 0;
+  int64_t code_off[STF_MAX_LEVELS];
+  for (int L = 0; L < t->levels; ++L) {
+    const int w = d->dims[0] >> L > 0 ? d->dims[0] >> L : 1;
+    const int h = d->dims[1] >> L > 0 ? d->dims[1] >> L : 1;
+    t->level_off[L] = texels;           // texel offsets first (staging pyramid)
+    t->level_w[L] = w;
+    t->level_h[L] = h;
+    t->blocks_w[L] = (w + 7) / 8;
+    code_off[L] = words;
+    texels += (int64_t)w * h;
+    words += (int64_t)t->blocks_w[L] * ((h + 7) / 8) * C;
+  }
+  const int64_t nvals = texels * C;
+  cudaError_t e = dev_alloc(&t->d_texels, (size_t)words * 4);
+  if (e != cudaSuccess) return fail_cuda(e, "code allocation");
+  t->bytes += words * 4;
+  float* tmp = nullptr;
+  double* scratch = nullptr;
+  e = dev_alloc((void**)&tmp, (size_t)nvals * 4);
+  if (e != cudaSuccess) return fail_cuda(e, "staging allocation");
+  e = dev_alloc((void**)&scratch, (size_t)(words * 6 + 8) * 8);
+  if (e != cudaSuccess) {
+    cudaFree(tmp);
+    return fail_cuda(e, "encoder scratch allocation");
+  }
+  const cudaMemcpyKind kind = d->data_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  const int64_t given = d->generate_mips ? (int64_t)t->level_w[0] * t->level_h[0] * C : nvals;
+  e = cudaMemcpyAsync(tmp, d->data, (size_t)given * 4, kind, s);
+  if (e == cudaSuccess && d->generate_mips) {
+    for (int L = 1; L < t->levels && e == cudaSuccess; ++L)
+      e = launch_box_mip(tmp + t->level_off[L - 1] * C, tmp + t->level_off[L] * C,
+                         t->level_w[L - 1], t->level_h[L - 1], C, s);
+  }
+  double range[8] = {0};
+  if (e == cudaSuccess)
+    e = launch_dct_encode(tmp, t->level_off, t->level_w, t->level_h, t->levels, C,
+                          (uint32_t*)t->d_texels, code_off, scratch, range, s);
+  cudaFree(tmp);
+  cudaFree(scratch);
+  if (e != cudaSuccess) return fail_cuda(e, "DCT encode");
+  for (int L = 0; L < t->levels; ++L) t->level_off[L] = code_off[L];
+  for (int c = 0; c < 8; ++c) t->ac_step[c] = c < C ? (float)(range[c] / 15.0) : 0.0f;
+  const double pi = 3.14159265358979323846;
+  t->dct_k[0] = (float)std::sqrt(0.125);
+  for (int i = 0; i < 4; ++i) t->dct_k[1 + i] = (float)(0.5 * std::cos((2 * i + 1) * pi / 16.0));
+  t->dct_k[5] = (float)(0.5 * std::cos(pi / 8.0));
+  t->dct_k[6] = (float)(0.5 * std::cos(3.0 * pi / 8.0));
+  return STF_OK;
+}
+
 static stf_status create_grid(stf_texture_s* t, const stf_texture_desc* d, cudaStream_t s) {
+  if (d->format == STF_FMT_DCT6) return create_dct(t, d, s);
   const int C = t->channels;
   const size_t es = d->format == STF_FMT_F16 ? 2 : 4;
   int64_t total = 0;
@@ -186,8 +244,8 @@ stf_status stf_create_texture(const stf_texture_desc* d, void* stream, stf_textu
       if (W <= 0 || H <= 0) st = fail(STF_ERR_INVALID_ARGUMENT, "2D texture needs dims > 0");
       else if (d->channels != 1 && d->channels != 2 && d->channels != 4 && d->channels != 8)
         st = fail(STF_ERR_INVALID_ARGUMENT, "2D texture channels must be 1, 2, 4 or 8");
-      else if (d->format != STF_FMT_F32 && d->format != STF_FMT_F16)
-        st = fail(STF_ERR_INVALID_ARGUMENT, "2D texture format must be F32 or F16");
+      else if (d->format != STF_FMT_F32 && d->format != STF_FMT_F16 && d->format != STF_FMT_DCT6)
+        st = fail(STF_ERR_INVALID_ARGUMENT, "2D texture format must be F32, F16 or DCT6");
       else if (d->mip_levels < 1 || d->mip_levels > STF_MAX_LEVELS || d->mip_levels > maxlev)
         st = fail(STF_ERR_INVALID_ARGUMENT, "mip_levels %d outside [1, %d]", d->mip_levels,
                   maxlev < STF_MAX_LEVELS ? maxlev : STF_MAX_LEVELS);
@@ -329,7 +387,10 @@ Tex2DView view2d(const stf_texture_s* t) {
     v.level_off[L] = t->level_off[L];
     v.level_w[L] = t->level_w[L];
     v.level_h[L] = t->level_h[L];
+    v.blocks_w[L] = t->blocks_w[L];
   }
+  for (int c = 0; c < 8; ++c) v.ac_step[c] = t->ac_step[c];
+  for (int k = 0; k < 7; ++k) v.dct_k[k] = t->dct_k[k];
   return v;
 }
 
@@ -355,6 +416,40 @@ stf_status dispatch(Op op, stf_texture t, int filter, const LookupArgs& a, cudaS
       break;
   }
   return e == cudaSuccess ? STF_OK : fail_cuda(e, "lookup launch");
+}
+
+// Triplanar lookups (Section 5.2): positions and normals, n x 3 floats each.
+stf_status triplanar(Op op, stf_texture t, const stf_lookup_params* p, const float* pos,
+                     const float* normal, const float* lod, int64_t n, float scale, float* out,
+                     int32_t* taps, cudaStream_t s) {
+  if (!handle_ok(t)) return fail(STF_ERR_INVALID_HANDLE, "unknown texture handle");
+  if (t->kind != STF_KIND_TEX2D) return fail(STF_ERR_UNSUPPORTED, "triplanar lookups need a 2D texture");
+  if (!p) return fail(STF_ERR_INVALID_ARGUMENT, "params is NULL");
+  if (n < 0) return fail(STF_ERR_INVALID_ARGUMENT, "n < 0");
+  if (p->filter < STF_FILTER_LINEAR || p->filter > STF_FILTER_FIS_GAUSSIAN)
+    return fail(STF_ERR_INVALID_ARGUMENT, "unknown filter %d", p->filter);
+  if (p->filter == STF_FILTER_CATMULL_ROM_POSITIVIZED)
+    return fail(STF_ERR_UNSUPPORTED, "positivized filtering is not offered for triplanar lookups");
+  if (p->filter == STF_FILTER_FIS_GAUSSIAN &&
+      !(p->filter_width > 0.0f && p->filter_width <= STF_FIS_MAX_WIDTH))
+    return fail(STF_ERR_INVALID_ARGUMENT, "filter_width %g outside (0, %g]", (double)p->filter_width,
+                (double)STF_FIS_MAX_WIDTH);
+  if (p->level_mode != STF_LEVEL_NEAREST && p->level_mode != STF_LEVEL_STOCHASTIC)
+    return fail(STF_ERR_INVALID_ARGUMENT, "unknown level mode %d", p->level_mode);
+  if (p->bin_queries) return fail(STF_ERR_UNSUPPORTED, "triplanar lookups are not binned");
+  if (!std::isfinite(scale)) return fail(STF_ERR_INVALID_ARGUMENT, "scale is not finite");
+  if (n == 0) return STF_OK;
+  if (!pos || !normal || !out) return fail(STF_ERR_INVALID_ARGUMENT, "pos, normal or out is NULL");
+  if ((uintptr_t)pos % 4 || (uintptr_t)normal % 4 || (lod && (uintptr_t)lod % 4))
+    return fail(STF_ERR_INVALID_ARGUMENT, "pos, normal or lod not 4-byte aligned");
+  const size_t oa = t->channels >= 4 ? 16 : (size_t)t->channels * 4;
+  if ((uintptr_t)out % oa) return fail(STF_ERR_INVALID_ARGUMENT, "out not %zu-byte aligned", oa);
+  if (taps && (uintptr_t)taps % 16) return fail(STF_ERR_INVALID_ARGUMENT, "taps not 16-byte aligned");
+  LookupArgs a = make_args(p, pos, lod, n, out, taps);
+  a.reuse = 0;
+  a.normals = normal;
+  a.tri_scale = scale;
+  return dispatch(op, t, p->filter, a, s);
 }
 
 }  // namespace stf
@@ -392,6 +487,22 @@ stf_status stf_lookup_accumulate(stf_texture t, const stf_lookup_params* p, cons
   a.sum = d_sum;
   a.sumsq = d_sumsq;
   return dispatch(OP_ACCUMULATE, t, p->filter, a, (cudaStream_t)stream);
+}
+
+
+stf_status stf_lookup_batch_triplanar(stf_texture t, const stf_lookup_params* p, const float* d_pos,
+                                      const float* d_normal, const float* d_lod, int64_t n,
+                                      float scale, float* d_out, int32_t* d_taps, void* stream) {
+  return stf::triplanar(stf::OP_STOCHASTIC, t, p, d_pos, d_normal, d_lod, n, scale, d_out, d_taps,
+                        (cudaStream_t)stream);
+}
+
+stf_status stf_lookup_batch_triplanar_deterministic(stf_texture t, const stf_lookup_params* p,
+                                                    const float* d_pos, const float* d_normal,
+                                                    const float* d_lod, int64_t n, float scale,
+                                                    float* d_out, void* stream) {
+  return stf::triplanar(stf::OP_DETERMINISTIC, t, p, d_pos, d_normal, d_lod, n, scale, d_out, nullptr,
+                        (cudaStream_t)stream);
 }
 
 }  // extern "C"

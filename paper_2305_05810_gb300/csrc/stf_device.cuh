@@ -174,11 +174,16 @@ __device__ __forceinline__ float pick_taps(const float* x, const float* u, int* 
 
 // ---------------------------------------------------------------- views
 struct Tex2DView {
-  const void* texels;     // storage format, [level][y][x][c]
-  int64_t level_off[STF_MAX_LEVELS];   // element offset (in texels) of each level
+  const void* texels;     // storage format, [level][y][x][c]; DCT6: [level][by][bx][c] words
+  int64_t level_off[STF_MAX_LEVELS];   // offset of each level: texels, or DCT6 code words
   int32_t level_w[STF_MAX_LEVELS];
   int32_t level_h[STF_MAX_LEVELS];
   int32_t levels;
+  // DCT6 only
+  int32_t blocks_w[STF_MAX_LEVELS];    // blocks per row of each level
+  float ac_step[8];                    // value of one AC code step per channel, R_c / 15
+  // a(0) = sqrt(1/8); (1/2) cos((2i+1) pi/16), i = 0..3; (1/2) cos(pi/8), (1/2) cos(3 pi/8)
+  float dct_k[7];
 };
 
 struct Dense3DView {
@@ -205,6 +210,9 @@ struct LookupArgs {
   // Binned calls: coords/lod are in binned order and perm[i] is the caller's index
   // of binned query i (it keys the generator and picks the output slot).
   const uint32_t* perm;
+  // Triplanar calls: coords are positions (n x 3), normals n x 3, uv = scale * p.
+  const float* normals;
+  float tri_scale;
 };
 
 __device__ __forceinline__ int64_t query_slot(const LookupArgs& a, int64_t i) {
@@ -283,7 +291,7 @@ __device__ __forceinline__ void pick_positivized(const float* x, const float* up
 }
 
 // ---------------------------------------------------------------- filter importance sampling
-// Section 3, "Filter Importance Sampling": an offset s is drawn from a density and
+// Section 4.4, "Filter Importance Sampling": an offset s is drawn from a density and
 // the texel nearest to x + s, floor(x + s + 1/2), is fetched unscaled.  Taking the
 // nearest texel convolves the density with a unit box; that convolution is the
 // filter applied (a B-spline of one degree higher, or the box-blurred Gaussian).
@@ -446,6 +454,62 @@ template <int C> struct TexelIO<STF_FMT_F16, C> {
     }
   }
 };
+
+// ---------------------------------------------------------------- DCT6 texels
+// a(u) cos((2x+1) u pi / 16) for u = 0, 1, 2 from the seven stored constants, using
+// c1(7 - x) = -c1(x) and c2(7 - x) = c2(x) (only compile-time indices into the view).
+__device__ __forceinline__ void dct_basis(const Tex2DView& t, int x, float& c0, float& c1, float& c2) {
+  const bool lo = x < 4;
+  const int i = lo ? x : 7 - x;
+  const float m1 = i == 0 ? t.dct_k[1] : i == 1 ? t.dct_k[2] : i == 2 ? t.dct_k[3] : t.dct_k[4];
+  c0 = t.dct_k[0];
+  c1 = lo ? m1 : -m1;
+  const float m2 = (i == 0 || i == 3) ? t.dct_k[5] : t.dct_k[6];
+  c2 = i < 2 ? m2 : -m2;
+}
+
+__device__ __forceinline__ float dct_ac(uint32_t w, int j) {
+  return (float)(((int32_t)(w << (20 - 5 * j))) >> 27);     // 5-bit field, sign-extended
+}
+
+// Texel (x, y) of level L, clamped to the level: f = sum over the six coefficients of
+// value * basis(x) * basis(y), float32.
+template <int C>
+__device__ __forceinline__ void dct_texel(const Tex2DView& t, int L, int x, int y, float* v) {
+  const uint32_t* p = reinterpret_cast<const uint32_t*>(t.texels) + t.level_off[L] +
+                      ((int64_t)(y >> 3) * t.blocks_w[L] + (x >> 3)) * C;
+  uint32_t w[C];
+  if constexpr (C % 4 == 0) {
+#pragma unroll
+    for (int k = 0; k < C / 4; ++k) {
+      const uint4 q = __ldg(reinterpret_cast<const uint4*>(p) + k);
+      w[4 * k] = q.x; w[4 * k + 1] = q.y; w[4 * k + 2] = q.z; w[4 * k + 3] = q.w;
+    }
+  } else if constexpr (C == 2) {
+    const uint2 q = __ldg(reinterpret_cast<const uint2*>(p));
+    w[0] = q.x; w[1] = q.y;
+  } else {
+    w[0] = __ldg(p);
+  }
+  float x0, x1, x2, y0, y1, y2;
+  dct_basis(t, x & 7, x0, x1, x2);
+  dct_basis(t, y & 7, y0, y1, y2);
+  const float b[6] = {x0 * y0, x1 * y0, x0 * y1, x2 * y0, x1 * y1, x0 * y2};
+#pragma unroll
+  for (int c = 0; c < C; ++c) {
+    float f = (float)(w[c] & 127u) * (8.0f / 127.0f) * b[0];
+#pragma unroll
+    for (int j = 0; j < 5; ++j) f = fmaf(dct_ac(w[c], j) * t.ac_step[c], b[j + 1], f);
+    v[c] = f;
+  }
+}
+
+// Texel (cx, cy) of level L, already clamped to the level, in any 2D storage format.
+template <int FMT, int C>
+__device__ __forceinline__ void fetch2d(const Tex2DView& t, int L, int cx, int cy, float* v) {
+  if constexpr (FMT == STF_FMT_DCT6) dct_texel<C>(t, L, cx, cy, v);
+  else TexelIO<FMT, C>::load(t.texels, t.level_off[L] + (int64_t)cy * t.level_w[L] + cx, v);
+}
 
 template <int C>
 __device__ __forceinline__ void store_out(float* out, int64_t i, const float* v) {

@@ -6,7 +6,7 @@
 // axis, lengthened to major / max_anisotropy when the ratio exceeds the limit, and
 // lod = log2(minor).
 //
-// EWA (Section 5.3 and the stochastic EWA listing of Appendix B, which samples
+// EWA (Section 4.2 and the stochastic EWA listing of Appendix B, which samples
 // pbrt's elliptically weighted average): at level L the filter is a Gaussian table
 // over the ellipse Q(s, t) = A s^2 + B s t + C t^2 < 1, (A, B, C) / F being the
 // inverse of d0 d0^T + d1 d1^T + I.  The stochastic form draws one texel of the
@@ -25,6 +25,7 @@ namespace stf {
 
 constexpr int kEwaLut = 128;
 constexpr int kEwaMaxSpan = 4096;   // bounding boxes are far smaller (see ewa_ellipse)
+constexpr int kEwaRows = 48;        // rows whose running sums the stochastic search caches
 
 // Gaussian weight table exp(-2 r) - exp(-2), r = i / 127, rounded to float32.  It is
 // passed by value and staged in shared memory by every block.
@@ -185,18 +186,29 @@ __global__ void __launch_bounds__(256) k_ewa(Tex2DView t, EwaArgs a, EwaTable ta
         if (!ewa_span_ok(e)) {
           atomicOr(a.status, STF_DEV_BAD_NODE);
         } else {
+          // Pass 1: the running float32 sum, recorded at the end of each of the first
+          // kEwaRows rows.  Pass 2 resumes from the last recorded value below u S, so it
+          // rescans one row in the common case and repeats exactly the same additions.
           float S = 0.0f;
+          float row_end[kEwaRows];
           for (int it = e.t0; it <= e.t1; ++it) {
             const float tt = __fsub_rn((float)it, e.st_t);
             for (int is = e.s0; is <= e.s1; ++is) {
               const float w = ewa_weight(e, lut, is, tt);
               if (w > 0.0f) S = __fadd_rn(S, w);
             }
+            if (it - e.t0 < kEwaRows) row_end[it - e.t0] = S;
           }
           const float us = __fmul_rn(unit24(r.x), S);
           float Cs = 0.0f;
+          int start = e.t0;
+          const int cached = min(e.t1 - e.t0 + 1, kEwaRows);
+          for (int k = 0; k < cached && row_end[k] <= us; ++k) {
+            Cs = row_end[k];
+            start = e.t0 + k + 1;
+          }
           int cs = INT_MIN, ct = 0;
-          for (int it = e.t0; it <= e.t1 && cs == INT_MIN; ++it) {
+          for (int it = start; it <= e.t1 && cs == INT_MIN; ++it) {
             const float tt = __fsub_rn((float)it, e.st_t);
             for (int is = e.s0; is <= e.s1; ++is) {
               const float w = ewa_weight(e, lut, is, tt);
@@ -214,8 +226,7 @@ __global__ void __launch_bounds__(256) k_ewa(Tex2DView t, EwaArgs a, EwaTable ta
             atomicOr(a.status, STF_DEV_BAD_NODE);   // cannot happen: us < S
           } else {
             tap = make_int4(cs, ct, 0, L0);
-            TexelIO<FMT, C>::load(t.texels, t.level_off[L0] + (int64_t)min(max(ct, 0), HL - 1) * WL +
-                                                min(max(cs, 0), WL - 1), v);
+            fetch2d<FMT, C>(t, L0, min(max(cs, 0), WL - 1), min(max(ct, 0), HL - 1), v);
           }
         }
       } else {
@@ -242,12 +253,12 @@ __global__ void __launch_bounds__(256) k_ewa(Tex2DView t, EwaArgs a, EwaTable ta
           for (int c = 0; c < C; ++c) acc[c] = 0.0f;
           for (int it = e.t0; it <= e.t1; ++it) {
             const float tt = __fsub_rn((float)it, e.st_t);
-            const int64_t row = t.level_off[L] + (int64_t)min(max(it, 0), HL - 1) * WL;
+            const int cy = min(max(it, 0), HL - 1);
             for (int is = e.s0; is <= e.s1; ++is) {
               const float w = ewa_weight(e, lut, is, tt);
               if (w > 0.0f) {
                 float tv[C];
-                TexelIO<FMT, C>::load(t.texels, row + min(max(is, 0), WL - 1), tv);
+                fetch2d<FMT, C>(t, L, min(max(is, 0), WL - 1), cy, tv);
                 S = __fadd_rn(S, w);
 #pragma unroll
                 for (int c = 0; c < C; ++c) acc[c] = fmaf(w, tv[c], acc[c]);
@@ -298,6 +309,13 @@ static cudaError_t launch_ewa(bool stoch, int fmt, int c, const Tex2DView& t, co
       case 2: return run_ewa<STF_FMT_F16, 2>(stoch, t, a, s);
       case 4: return run_ewa<STF_FMT_F16, 4>(stoch, t, a, s);
       case 8: return run_ewa<STF_FMT_F16, 8>(stoch, t, a, s);
+    }
+  } else if (fmt == STF_FMT_DCT6) {
+    switch (c) {
+      case 1: return run_ewa<STF_FMT_DCT6, 1>(stoch, t, a, s);
+      case 2: return run_ewa<STF_FMT_DCT6, 2>(stoch, t, a, s);
+      case 4: return run_ewa<STF_FMT_DCT6, 4>(stoch, t, a, s);
+      case 8: return run_ewa<STF_FMT_DCT6, 8>(stoch, t, a, s);
     }
   }
   return cudaErrorInvalidValue;

@@ -11,6 +11,9 @@ stf_status fail_cuda(cudaError_t e, const char* what);
 cudaError_t dev_alloc(void** p, size_t bytes);
 bool handle_ok(stf_texture t);
 stf_status dispatch(Op op, stf_texture t, int filter, const LookupArgs& a, cudaStream_t s);
+stf_status triplanar(Op op, stf_texture t, const stf_lookup_params* p, const float* pos,
+                     const float* normal, const float* lod, int64_t n, float scale, float* out,
+                     int32_t* taps, cudaStream_t s);
 stf_status check_lookup(stf_texture t, const stf_lookup_params* p, const float* coords,
                         const float* lod, int64_t n, const void* out);
 Tex2DView view2d(const stf_texture_s* t);

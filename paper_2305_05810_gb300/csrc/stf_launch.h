@@ -12,6 +12,12 @@ int grid_blocks(int64_t n, int threads);   // grid size for a grid-stride launch
 
 cudaError_t launch_tex2d(Op op, int filter, int fmt, int channels, const Tex2DView& t,
                          const LookupArgs& a, cudaStream_t s);
+cudaError_t launch_tex2d_f32(Op op, int filter, int channels, const Tex2DView& t,
+                             const LookupArgs& a, cudaStream_t s);
+cudaError_t launch_tex2d_f16(Op op, int filter, int channels, const Tex2DView& t,
+                             const LookupArgs& a, cudaStream_t s);
+cudaError_t launch_tex2d_dct(Op op, int filter, int channels, const Tex2DView& t,
+                             const LookupArgs& a, cudaStream_t s);
 cudaError_t launch_dense3d(Op op, int filter, int fmt, const Dense3DView& g,
                            const LookupArgs& a, cudaStream_t s);
 cudaError_t launch_sparse3d(Op op, int filter, int fmt, const SparseDev& g,
@@ -20,5 +26,10 @@ cudaError_t launch_sparse3d(Op op, int filter, int fmt, const SparseDev& g,
 // Create-time kernels.
 cudaError_t launch_convert_f32(const float* src, void* dst, int fmt, int64_t n, cudaStream_t s);
 cudaError_t launch_box_mip(const float* src, float* dst, int w, int h, int c, cudaStream_t s);
+// DCT6 encoding of a float32 pyramid (levels at level_off texels of src, C channels):
+// codes at code_off words of dst, per-channel AC ranges R_c (float64, host) out.
+cudaError_t launch_dct_encode(const float* src, const int64_t* level_off, const int32_t* w,
+                              const int32_t* h, int levels, int C, uint32_t* dst,
+                              const int64_t* code_off, double* scratch, double* h_range, cudaStream_t s);
 
 }  // namespace stf

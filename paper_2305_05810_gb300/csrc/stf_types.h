@@ -61,9 +61,13 @@ struct stf_texture_s {
   float background;
   // 2D / dense texels in storage format
   void* d_texels;
-  int64_t level_off[STF_MAX_LEVELS];
+  int64_t level_off[STF_MAX_LEVELS];   // texels, or code words for DCT6
   int32_t level_w[STF_MAX_LEVELS];
   int32_t level_h[STF_MAX_LEVELS];
+  // DCT6: blocks per row, AC step per channel (R_c / 15), basis constants
+  int32_t blocks_w[STF_MAX_LEVELS];
+  float ac_step[8];
+  float dct_k[7];
   // sparse tree (one allocation, views into it)
   void* d_tree;
   stf::SparseDev sparse;

@@ -223,3 +223,14 @@ def plane_view(W=1920, H=1080, seed=7, fov_deg=60.0, height=0.04, pitch_deg=12.0
     uv = p[ok]
     grad = np.concatenate([px1[ok] - uv, py1[ok] - uv], axis=1)
     return uv.astype(np.float32), grad.astype(np.float32)
+
+
+def sphere_points(n, seed=8, centre=(0.5, 0.5, 0.5), radius=0.45):
+    """Surface points of a sphere with their unit normals (triplanar-mapping queries):
+    directions uniform on the sphere (normalised Gaussian vectors).  Returns
+    (positions (n, 3), normals (n, 3)) float32."""
+    rng = np.random.default_rng(seed)
+    d = rng.standard_normal((n, 3))
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    p = np.asarray(centre)[None] + radius * d
+    return p.astype(np.float32), d.astype(np.float32)

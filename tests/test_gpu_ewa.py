@@ -1,4 +1,4 @@
-"""GPU parity for the anisotropic level of detail and EWA lookups (Sections 5.2, 5.3;
+"""GPU parity for the anisotropic level of detail and EWA lookups (Sections 4.2, 5.2;
 Appendix B) through the C ABI against the float32-decision / float64-value oracle
 (`oracle/ewa.py`).
 

@@ -1,4 +1,4 @@
-"""GPU parity for filter importance sampling (Section 3, "Filter Importance
+"""GPU parity for filter importance sampling (Section 4.4, "Filter Importance
 Sampling") through the C ABI against the float64 oracle (`oracle/fis.py`).
 
 Bar: the B-spline FIS index is computed exactly on both sides (integer arithmetic

@@ -1,4 +1,4 @@
-"""Pins of the filter-importance-sampling oracle (Section 3, "Filter Importance
+"""Pins of the filter-importance-sampling oracle (Section 4.4, "Filter Importance
 Sampling") against facts that do not come from the oracle itself: exhaustive and
 lattice enumeration of the variates against the B-spline kernels of
 `oracle.kernels`, closed-form Gaussian moments, numerical integration of the
@@ -24,7 +24,7 @@ def _xs():
 def test_linear_fis_exhaustive_over_all_variates():
     """n = 1 (uniform jitter): over all 2^24 variates the upper tap's frequency is the
     tent weight f, to the 2^-24 resolution of the variates (Hofmann et al.'s
-    stochastic trilinear, Section 3)."""
+    stochastic trilinear, Section 4.4)."""
     u = np.arange(1 << 24, dtype=np.float64) * 2.0 ** -24
     for x in _xs():
         idx, _ = fis.bspline_nearest(np.full(u.shape, x, dtype=np.float32), [u])
