@@ -587,6 +587,20 @@ def run_dct(args):
                 "h2d_bytes_per_step": n * 12, "d2h_bytes_per_step": n * 4 * C},
         "gpu_launches": args.warmup + args.steps, "clocks": clk.summary(), "extras": extras,
     }
+    if not args.no_cpu_baseline:
+        # the oracle's float64 encoder on the same pyramid (set-up, untimed), then its
+        # stochastic trilinear lookups on the first 20,000 queries (timed)
+        from oracle import dct as odct
+        from oracle import filters
+        lv = [p.astype(np.float64) for p in synth.box_levels(base, levels)]
+        ref = odct.DCTTexture2D(lv)
+        m = 20000
+        lod_h = lod.cpu().numpy()
+        t0 = time.perf_counter()
+        filters.lookup_2d(ref, uv_h[:m], lod_h[:m], "linear", stochastic_form=True, seed=2024)
+        dt = time.perf_counter() - t0
+        line["cpu_baseline"] = {"value": m / dt, "unit": "lookups/s", "cores": 1, "kind": "oracle",
+                                "sample": "first %d queries, stochastic trilinear on the DCT texture" % m}
     print(json.dumps(line), flush=True)
     tex.close()
     return 0
@@ -720,6 +734,22 @@ def run_ours(args):
                                 "ms_p50": pct(p2, 50), "ms_p99": pct(p2, 99)}
             except stf.StfError as e:
                 extras[name] = {"unavailable": str(e)}
+        if w["name"] == "tex2d":
+            # the 65,536-query configuration: per-launch latency over 1000 launches, and the
+            # 4096-sample sweep (268M lookups, float64 accumulators) as one launch
+            m = 1 << 16
+            p65 = stf.make_params(filt, seed=2024)
+            lat, _ = time_steps(torch, lambda: stf.stf_lookup_batch(tex.handle, p65, coords, None, m, out,
+                                                                     None, stream), 1000, 10, stream)
+            extras["c1_65536_queries_launch_ms"] = {"p50": pct(lat, 50), "p99": pct(lat, 99),
+                                                    "lookups_per_s": m / (statistics.mean(lat) / 1000.0),
+                                                    "l2": "inputs L2-resident (a latency figure)"}
+            s1 = torch.empty((m, C), dtype=torch.float64, device=dev)
+            s2 = torch.empty_like(s1)
+            sweep = lambda: stf.stf_lookup_accumulate(tex.handle, p65, coords, None, m, 4096, s1, s2, stream)
+            ps, ts = time_steps(torch, sweep, 3, 1, stream)
+            extras["c1_4096_sample_sweep"] = {"lookups_per_s": m * 4096 * len(ps) / (ts / 1000.0),
+                                              "ms": statistics.mean(ps)}
         det = extras.get("deterministic_" + filt, {})
         if "lookups_per_s" in det:
             extras["speedup_vs_deterministic"] = value / world / det["lookups_per_s"]

@@ -235,8 +235,8 @@ __device__ __forceinline__ NeuralPick neural_pick(const NeuralDev& nd, const Loo
 
 namespace tc {
 
-constexpr int ROWS = 128;            // queries per tile = threads per CTA
-constexpr int TMEM_COLS = 128;       // D1/D2 in columns 0..63, D3 in 64..79
+constexpr int ROWS = 128;            // queries per tile = threads per group
+constexpr int TMEM_COLS = 128;       // 64 columns per group: D1/D2 in 0..63, D3 in 0..15
 constexpr int A1_BYTES = ROWS * 16 * 2, A2_BYTES = ROWS * 64 * 2;
 constexpr int B1_BYTES = 64 * 16 * 2, B2_BYTES = 64 * 64 * 2, B3_BYTES = 16 * 64 * 2;
 
@@ -307,17 +307,20 @@ __device__ __forceinline__ void tmem_ld<8>(uint32_t taddr, uint32_t* r) {
   asm volatile("tcgen05.wait::ld.sync.aligned;");
 }
 
+struct Group {                       // one tile in flight
+  unsigned char a1[A1_BYTES];
+  unsigned char a2[A2_BYTES];          // H1, then H2, then the staged output rows
+  uint64_t bar;
+  int abort;
+};
+
 struct Smem {
   unsigned char b1[B1_BYTES];
   unsigned char b2[B2_BYTES];
   unsigned char b3[B3_BYTES];
-  unsigned char a1[2][A1_BYTES];
-  unsigned char a2[A2_BYTES];
+  Group grp[2];
   float bias[nn::NBIAS];
-  float out[ROWS * 7];
-  uint64_t bar;
   uint32_t tmem;
-  int abort;
 };
 
 }  // namespace tc
@@ -346,34 +349,45 @@ __device__ __forceinline__ void tc_hidden(uint32_t taddr, const float* bias, uns
   }
 }
 
+// Named barrier of one 128-thread group.
+__device__ __forceinline__ void group_sync(int g) { asm volatile("bar.sync %0, 128;" ::"r"(1 + g) : "memory"); }
+
+// Two groups of 128 threads per CTA decode two tiles concurrently: each group owns an
+// A1/A2 tile pair, 64 tensor-memory columns (D1, D2, then D3 over the first 16 once D2
+// has been read), an mbarrier and a named barrier, and walks its own tile sequence;
+// while one group waits on its MMAs or its gathers the other computes.  The weights
+// are shared.  A group's A1 is refilled with the next tile's gather as soon as layer 1
+// has consumed it.
 template <int F>
-__global__ void __launch_bounds__(128) k_neural_stochastic_tc(NeuralDev nd, LookupArgs a) {
+__global__ void __launch_bounds__(256, 4) k_neural_stochastic_tc(NeuralDev nd, LookupArgs a) {
   extern __shared__ __align__(1024) unsigned char dyn[];
   tc::Smem& s = *reinterpret_cast<tc::Smem*>(dyn);
   const int tid = threadIdx.x, warp = tid >> 5;
+  const int g = tid >> 7, row = tid & 127;          // group, row of the group's tile
+  tc::Group& G = s.grp[g];
   // weights: binary16 images -> K-major no-swizzle B tiles (16-byte rows)
   {
     const uint4* img = reinterpret_cast<const uint4*>(nd.wimg);
-    for (int e = tid; e < 64 * 2; e += 128) {        // W1^T: n < 64, k chunks of 8 (< 16)
+    for (int e = tid; e < 64 * 2; e += 256) {        // W1^T: n < 64, k chunks of 8 (< 16)
       const int n = e >> 1, kc = e & 1;
       *reinterpret_cast<uint4*>(s.b1 + tc::off(n, 8 * kc, 16)) = __ldg(img + (nn::I_W1T + n * 24 + 8 * kc) / 8);
     }
-    for (int e = tid; e < 64 * 8; e += 128) {        // W2^T: n < 64, k chunks of 8 (< 64)
+    for (int e = tid; e < 64 * 8; e += 256) {        // W2^T: n < 64, k chunks of 8 (< 64)
       const int n = e >> 3, kc = e & 7;
       *reinterpret_cast<uint4*>(s.b2 + tc::off(n, 8 * kc, 64)) = __ldg(img + (nn::I_W2T + n * 72 + 8 * kc) / 8);
     }
-    for (int e = tid; e < 16 * 8; e += 128) {        // W3^T: n < 16 (rows >= 8 zero)
+    for (int e = tid; e < 16 * 8; e += 256) {        // W3^T: n < 16 (rows >= 8 zero)
       const int n = e >> 3, kc = e & 7;
       *reinterpret_cast<uint4*>(s.b3 + tc::off(n, 8 * kc, 64)) =
           n < 8 ? __ldg(img + (nn::I_W3T + n * 72 + 8 * kc) / 8) : make_uint4(0, 0, 0, 0);
     }
-    for (int k = tid; k < nn::NBIAS; k += 128) s.bias[k] = __ldg(nd.bias + k);
-    for (int b = 0; b < 2; ++b)                      // latent columns 8..15 of A1 stay zero
-      *reinterpret_cast<uint4*>(s.a1[b] + tc::off(tid, 8, 16)) = make_uint4(0, 0, 0, 0);
+    for (int k = tid; k < nn::NBIAS; k += 256) s.bias[k] = __ldg(nd.bias + k);
+    // latent columns 8..15 of A1 stay zero
+    *reinterpret_cast<uint4*>(G.a1 + tc::off(row, 8, 16)) = make_uint4(0, 0, 0, 0);
   }
-  if (tid == 0) {
-    s.abort = 0;
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"((uint32_t)__cvta_generic_to_shared(&s.bar)));
+  if (row == 0) {
+    G.abort = 0;
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"((uint32_t)__cvta_generic_to_shared(&G.bar)));
     asm volatile("fence.mbarrier_init.release.cluster;");
   }
   if (warp == 0) {
@@ -384,84 +398,82 @@ __global__ void __launch_bounds__(128) k_neural_stochastic_tc(NeuralDev nd, Look
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;");
-  const uint32_t tmem = s.tmem;
-  const uint32_t trow = tmem + ((uint32_t)(32 * warp) << 16);   // this warp's 32 lanes
+  const uint32_t tmem = s.tmem + 64 * g;                          // this group's columns
+  const uint32_t trow = tmem + ((uint32_t)(32 * (warp & 3)) << 16);  // this warp's lanes
   uint32_t parity = 0;
   const int64_t ntiles = (a.n + tc::ROWS - 1) / tc::ROWS;
-  int64_t tile = blockIdx.x;
-  int buf = 0;
+  const int64_t step = 2 * (int64_t)gridDim.x;
+  int64_t tile = 2 * (int64_t)blockIdx.x + g;
+  uint4* arow = reinterpret_cast<uint4*>(G.a1 + tc::off(row, 0, 16));
   NeuralPick cur;
-  if (tile < ntiles)
-    cur = neural_pick<F>(nd, a, tile * tc::ROWS + tid, reinterpret_cast<uint4*>(s.a1[0] + tc::off(tid, 0, 16)));
+  if (tile < ntiles) cur = neural_pick<F>(nd, a, tile * tc::ROWS + row, arow);
   cp_async_commit();
-  for (; tile < ntiles; tile += gridDim.x) {
-    const int64_t next = tile + gridDim.x;
+  for (; tile < ntiles; tile += step) {
+    cp_async_wait<0>();
+    uint4 fb = make_uint4(0, 0, 0, 0);
+    if (cur.mode == 2) fb = *arow;                   // stored fallback texel (own row)
+    asm volatile("fence.proxy.async.shared::cta;");
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    group_sync(g);
+    // layer 1: D[0, 64) = A1 (128 x 16) * W1 (16 x 64); one thread issues and waits
+    if (row == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;");
+      tc::mma(tmem, tc::desc(G.a1, 16), tc::desc(s.b1, 16), tc::idesc(128, 64), 0);
+      tc::commit(&G.bar);
+      if (!tc::wait_bar(&G.bar, parity)) G.abort = 1;
+    }
+    parity ^= 1;
+    group_sync(g);
+    if (G.abort) break;
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    // A1 is free: start the next tile's gather
+    const int64_t next = tile + step;
     NeuralPick nxt;
-    if (next < ntiles)
-      nxt = neural_pick<F>(nd, a, next * tc::ROWS + tid,
-                           reinterpret_cast<uint4*>(s.a1[buf ^ 1] + tc::off(tid, 0, 16)));
+    if (next < ntiles) nxt = neural_pick<F>(nd, a, next * tc::ROWS + row, arow);
     cp_async_commit();
-    cp_async_wait<1>();
+    tc_hidden(trow, s.bias, G.a2, row);
     asm volatile("fence.proxy.async.shared::cta;");
     asm volatile("tcgen05.fence::before_thread_sync;");
-    __syncthreads();
-    if (s.abort) break;
-    // layer 1: D[0, 64) = A1 (128 x 16) * W1 (16 x 64)
-    // one thread issues and waits; the others park in the barrier without issuing
-    if (tid == 0) {
-      asm volatile("tcgen05.fence::after_thread_sync;");
-      tc::mma(tmem, tc::desc(s.a1[buf], 16), tc::desc(s.b1, 16), tc::idesc(128, 64), 0);
-      tc::commit(&s.bar);
-      if (!tc::wait_bar(&s.bar, parity)) s.abort = 1;
-    }
-    parity ^= 1;
-    __syncthreads();
-    if (s.abort) break;
-    asm volatile("tcgen05.fence::after_thread_sync;");
-    tc_hidden(trow, s.bias, s.a2, tid);
-    asm volatile("fence.proxy.async.shared::cta;");
-    asm volatile("tcgen05.fence::before_thread_sync;");
-    __syncthreads();
+    group_sync(g);
     // layer 2: D[0, 64) = H1 (128 x 64) * W2 (64 x 64)
-    if (tid == 0) {
+    if (row == 0) {
       asm volatile("tcgen05.fence::after_thread_sync;");
 #pragma unroll
       for (int kk = 0; kk < 4; ++kk)
-        tc::mma(tmem, tc::desc(s.a2 + kk * 256, 64), tc::desc(s.b2 + kk * 256, 64), tc::idesc(128, 64), kk);
-      tc::commit(&s.bar);
-      if (!tc::wait_bar(&s.bar, parity)) s.abort = 1;
+        tc::mma(tmem, tc::desc(G.a2 + kk * 256, 64), tc::desc(s.b2 + kk * 256, 64), tc::idesc(128, 64), kk);
+      tc::commit(&G.bar);
+      if (!tc::wait_bar(&G.bar, parity)) G.abort = 1;
     }
     parity ^= 1;
-    __syncthreads();
-    if (s.abort) break;
+    group_sync(g);
+    if (G.abort) break;
     asm volatile("tcgen05.fence::after_thread_sync;");
-    tc_hidden(trow, s.bias + 64, s.a2, tid);
+    tc_hidden(trow, s.bias + 64, G.a2, row);
     asm volatile("fence.proxy.async.shared::cta;");
     asm volatile("tcgen05.fence::before_thread_sync;");
-    __syncthreads();
-    // layer 3: D[64, 80) = H2 (128 x 64) * W3 (64 x 16)
-    if (tid == 0) {
+    group_sync(g);
+    // layer 3: D[0, 16) = H2 (128 x 64) * W3 (64 x 16); D2 has been read
+    if (row == 0) {
       asm volatile("tcgen05.fence::after_thread_sync;");
 #pragma unroll
       for (int kk = 0; kk < 4; ++kk)
-        tc::mma(tmem + 64, tc::desc(s.a2 + kk * 256, 64), tc::desc(s.b3 + kk * 256, 64), tc::idesc(128, 16), kk);
-      tc::commit(&s.bar);
-      if (!tc::wait_bar(&s.bar, parity)) s.abort = 1;
+        tc::mma(tmem, tc::desc(G.a2 + kk * 256, 64), tc::desc(s.b3 + kk * 256, 64), tc::idesc(128, 16), kk);
+      tc::commit(&G.bar);
+      if (!tc::wait_bar(&G.bar, parity)) G.abort = 1;
     }
     parity ^= 1;
-    __syncthreads();
-    if (s.abort) break;
+    group_sync(g);
+    if (G.abort) break;
     asm volatile("tcgen05.fence::after_thread_sync;");
     float v[8];
     {
       uint32_t r[8];
-      tc::tmem_ld<8>(trow + 64, r);
+      tc::tmem_ld<8>(trow, r);
 #pragma unroll
       for (int k = 0; k < 7; ++k) v[k] = __uint_as_float(r[k]) + s.bias[128 + k];
     }
-    if (cur.mode == 2) {          // stored fallback texel, fetched into the A1 row
-      const uint4 t4 = *reinterpret_cast<const uint4*>(s.a1[buf] + tc::off(tid, 0, 16));
-      const uint32_t* tw = reinterpret_cast<const uint32_t*>(&t4);
+    if (cur.mode == 2) {
+      const uint32_t* tw = reinterpret_cast<const uint32_t*>(&fb);
 #pragma unroll
       for (int k = 0; k < 4; ++k) {
         const float2 f = unpack_h2(tw[k]);
@@ -474,28 +486,31 @@ __global__ void __launch_bounds__(128) k_neural_stochastic_tc(NeuralDev nd, Look
     }
 #pragma unroll
     for (int k = 0; k < 7; ++k) v[k] *= cur.sigma;
-    const int64_t i = tile * tc::ROWS + tid;
+    const int64_t i = tile * tc::ROWS + row;
     const bool live = i < a.n;
     if (a.perm == nullptr) {
+      // stage the tile's rows in A2 (free now) and store them coalesced
+      float* stage = reinterpret_cast<float*>(G.a2);
 #pragma unroll
-      for (int k = 0; k < 7; ++k) s.out[tid * 7 + k] = v[k];
-      __syncthreads();
+      for (int k = 0; k < 7; ++k) stage[row * 7 + k] = v[k];
+      group_sync(g);
       const int64_t nrows = min((int64_t)tc::ROWS, a.n - tile * tc::ROWS);
       float* dst = a.out + tile * tc::ROWS * 7;
-      for (int e = tid; e < nrows * 7; e += 128) dst[e] = s.out[e];
+      for (int e = row; e < nrows * 7; e += 128) dst[e] = stage[e];
     } else if (live) {
 #pragma unroll
       for (int k = 0; k < 7; ++k) a.out[cur.j * 7 + k] = v[k];
     }
     if (live && a.taps) reinterpret_cast<int4*>(a.taps)[cur.j] = cur.tap;
     cur = nxt;
-    buf ^= 1;
+    // the next iteration's first group barrier orders these reads of A2 before the
+    // next tile writes it
   }
   cp_async_wait<0>();
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
-  if (s.abort && tid == 0) atomicOr(nd.status, STF_DEV_MMA_TIMEOUT);
-  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "n"(tc::TMEM_COLS));
+  if (row == 0 && G.abort) atomicOr(nd.status, STF_DEV_MMA_TIMEOUT);
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(s.tmem), "n"(tc::TMEM_COLS));
 }
 
 // Deterministic: every tap of the filter window (at one level, or two blended by
@@ -993,9 +1008,10 @@ template <int F>
 static cudaError_t run_neural(Op op, const NeuralDev& nd, const LookupArgs& a, cudaStream_t s) {
   const int blocks = grid_blocks(a.n, 128);
   if (op == OP_STOCHASTIC) {
-    // 56 KiB of shared memory per CTA keeps at most 4 CTAs on an SM, so their
-    // 4 x 128 tensor-memory columns fit in the SM's 512
-    const int smem = (int)sizeof(tc::Smem) + 1024 > 56 * 1024 ? (int)sizeof(tc::Smem) + 1024 : 56 * 1024;
+    // at least 46 KiB of shared memory per CTA keeps at most 4 CTAs on an SM (228 KiB),
+    // so their 4 x 128 tensor-memory columns fit in the SM's 512 and no allocation waits
+    const int need = (int)sizeof(tc::Smem) + 1024;
+    const int smem = need > 46 * 1024 ? need : 46 * 1024;
     static bool attr = false;
     if (!attr) {
       cudaFuncSetAttribute(k_neural_stochastic_tc<F>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
@@ -1004,9 +1020,9 @@ static cudaError_t run_neural(Op op, const NeuralDev& nd, const LookupArgs& a, c
     int sms = 0, dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const int64_t tiles = (a.n + tc::ROWS - 1) / tc::ROWS;
-    const int grid = (int)(tiles < (int64_t)sms * 4 ? tiles : (int64_t)sms * 4);
-    k_neural_stochastic_tc<F><<<grid, 128, smem, s>>>(nd, a);
+    const int64_t pairs = ((a.n + tc::ROWS - 1) / tc::ROWS + 1) / 2;   // two tiles per CTA pass
+    const int grid = (int)(pairs < (int64_t)sms * 4 ? pairs : (int64_t)sms * 4);
+    k_neural_stochastic_tc<F><<<grid, 256, smem, s>>>(nd, a);
     return cudaGetLastError();
   }
   else if (op == OP_DETERMINISTIC) k_neural_deterministic<F><<<blocks, 128, 0, s>>>(nd, a);
