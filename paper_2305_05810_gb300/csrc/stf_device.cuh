@@ -36,27 +36,37 @@ __device__ __forceinline__ float unit24(uint32_t r) { return (float)(r >> 8) * 0
 // Weights of the taps floor(x) + OFF0 + k, k = 0..T-1, at fraction f = x - floor(x).
 template <int F> struct Filter;
 
-// Tent K1 (Appendix A): taps floor(x), floor(x)+1.
+// Tent K1 (Appendix A): taps floor(x), floor(x)+1.  CDF boundary (the weights sum to
+// exactly 1): C_0 = 1 - f.
 template <> struct Filter<STF_FILTER_LINEAR> {
   static constexpr int T = 2, OFF0 = 0;
-  static constexpr bool NONNEG = true;
+  static constexpr bool NONNEG = true, UNIT_SUM = true;
   __device__ __forceinline__ static void weights(float f, float* w) {
     w[0] = 1.0f - f;
     w[1] = f;
   }
+  __device__ __forceinline__ static void cdf(float f, float* c) { c[0] = 1.0f - f; }
 };
 
 // Cubic B-spline K_bs (Appendix A, "Convolutional"): with g = 1 - f the four taps
 // floor(x)-1 .. floor(x)+2 carry g^3/6, f^2(f/2 - 1) + 2/3, g^2(g/2 - 1) + 2/3, f^3/6.
+// The weights sum to exactly 1, so the interior CDF boundaries have closed forms:
+// C_0 = g^3/6, C_1 = w_0 + w_1 = (5 - 3f - 3f^2 + 2f^3)/6, C_2 = 1 - f^3/6.
 template <> struct Filter<STF_FILTER_BSPLINE3> {
   static constexpr int T = 4, OFF0 = -1;
-  static constexpr bool NONNEG = true;
+  static constexpr bool NONNEG = true, UNIT_SUM = true;
   __device__ __forceinline__ static void weights(float f, float* w) {
     const float g = 1.0f - f;
     w[0] = g * g * g * (1.0f / 6.0f);
     w[1] = fmaf(f * f, fmaf(0.5f, f, -1.0f), 2.0f / 3.0f);
     w[2] = fmaf(g * g, fmaf(0.5f, g, -1.0f), 2.0f / 3.0f);
     w[3] = f * f * f * (1.0f / 6.0f);
+  }
+  __device__ __forceinline__ static void cdf(float f, float* c) {
+    const float g = 1.0f - f, f2 = f * f;
+    c[0] = g * g * (g * (1.0f / 6.0f));
+    c[1] = fmaf(fmaf(fmaf(f, 1.0f / 3.0f, -0.5f), f, -0.5f), f, 5.0f / 6.0f);
+    c[2] = fmaf(f2, f * (-1.0f / 6.0f), 1.0f);
   }
 };
 
@@ -66,7 +76,7 @@ template <> struct Filter<STF_FILTER_BSPLINE3> {
 // g or f):  -f g^2/2,  g(1 + f(1 - 3f/2)),  f(1 + g(1 - 3g/2)),  -g f^2/2.
 template <> struct Filter<STF_FILTER_CATMULL_ROM> {
   static constexpr int T = 4, OFF0 = -1;
-  static constexpr bool NONNEG = false;
+  static constexpr bool NONNEG = false, UNIT_SUM = false;
   __device__ __forceinline__ static void weights(float f, float* w) {
     const float g = 1.0f - f;
     w[0] = -0.5f * f * g * g;
@@ -153,9 +163,28 @@ __device__ __forceinline__ bool prepare_coords(float* x) {
 // variate; with REUSE only u[0] is used and carried across axes by Eq. 4.
 // Returns the tap coordinates and the estimator's scale sigma (prod sign * S for
 // Catmull-Rom, exactly 1 for the non-negative kernels).
+// With independent variates and a kernel whose weights sum to exactly 1 (tent, cubic
+// B-spline) the tap is the number of closed-form CDF boundaries C_0 .. C_{T-2} that are
+// <= u (S = 1): the same rule, without summing the weights.  Its float32 boundaries
+// differ from the summed ones by a few 1e-8, inside the 1e-6 band in which the tap is
+// allowed to differ from the float64 reference.
 template <int F, int D, bool REUSE>
 __device__ __forceinline__ float pick_taps(const float* x, const float* u, int* idx) {
   using Fl = Filter<F>;
+  if constexpr (!REUSE && Fl::UNIT_SUM) {
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+      float f;
+      const int b = axis_base(x[a], f);
+      float c[Fl::T - 1];
+      Fl::cdf(f, c);
+      int k = 0;
+#pragma unroll
+      for (int j = 0; j < Fl::T - 1; ++j) k += (u[a] >= c[j]) ? 1 : 0;
+      idx[a] = b + Fl::OFF0 + k;
+    }
+    return 1.0f;
+  }
   float sigma = 1.0f;
   float uc = u[0];
 #pragma unroll
