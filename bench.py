@@ -54,7 +54,7 @@ def parse():
     ap.add_argument("--workload", default="dense",
                     choices=["dense", "tex2d", "sparse", "sparse_e4m3", "neural", "serving", "aniso",
                              "dct"])
-    ap.add_argument("--requests", type=int, default=600, help="serving: number of requests")
+    ap.add_argument("--requests", type=int, default=10000, help="serving: number of requests")
     ap.add_argument("--train-steps", type=int, default=400)
     ap.add_argument("--filter", default=None, choices=["linear", "bspline3", "catmull_rom"],
                     help="default: bspline3 (linear for the neural workload)")
@@ -734,6 +734,20 @@ def run_ours(args):
                                 "ms_p50": pct(p2, 50), "ms_p99": pct(p2, 99)}
             except stf.StfError as e:
                 extras[name] = {"unavailable": str(e)}
+        if w["name"] == "sparse_e4m3":
+            # storage error: deterministic tricubic on E4M3 leaves against the same lookups on
+            # the FP32 leaves (first 2^20 queries), in units of the voxel values' range
+            f32 = stf.Texture(stf.KIND_SPARSE3D, w["values"], fmt=stf.FMT_F32, leaf_origins=w["origins"])
+            m = 1 << 20
+            ref32 = torch.empty((m, 1), dtype=torch.float32, device=dev)
+            pq = stf.make_params(filt)
+            stf.stf_lookup_batch_deterministic(f32.handle, pq, coords, None, m, ref32, stream)
+            stf.stf_lookup_batch_deterministic(tex.handle, pq, coords, None, m, out, stream)
+            err = (out[:m] - ref32).abs()
+            rng = float(w["values"].max() - w["values"].min())
+            extras["e4m3_error_vs_fp32_leaves"] = {"max_abs": float(err.max()), "rms": float(err.pow(2).mean().sqrt()),
+                                                   "value_range": rng, "queries": m}
+            f32.close()
         if w["name"] == "tex2d":
             # the 65,536-query configuration: per-launch latency over 1000 launches, and the
             # 4096-sample sweep (268M lookups, float64 accumulators) as one launch
