@@ -776,13 +776,24 @@ def run_ours(args):
     d_lod = None if lod is None else torch.empty_like(lod)
     pe = stf.make_params(filt, seed=2024, level_mode=level_mode, query_offset=qoff)
 
+    # the package's host pipeline: chunks of 4M queries over three streams, so that the
+    # copies in both directions overlap the lookups
+    from paper_2305_05810_gb300.pipeline import HostPipeline
+    pipe = HostPipeline(tex, chunk=1 << 22, n_streams=3)
+
     def e2e_step():
+        pipe.lookup(pe, h_coords, h_out, h_lod)
+
+    def e2e_serial():
         d_in.copy_(h_coords, non_blocking=True)
         if d_lod is not None:
             d_lod.copy_(h_lod, non_blocking=True)
         stf.stf_lookup_batch(tex.handle, pe, d_in, d_lod, n, out, None, stream)
         h_out.copy_(out, non_blocking=True)
 
+    if not args.quick:
+        ps_, ts_ = time_steps(torch, e2e_serial, max(3, args.steps // 2), 2, stream)
+        extras["e2e_serial_one_stream"] = {"lookups_per_s": n * len(ps_) / (ts_ / 1000.0)}
     pe2, te2 = time_steps(torch, e2e_step, max(3, args.steps // 2), 2, stream, dist)
     t_e2e = torch.tensor([te2], dtype=torch.float64, device=dev)
     if dist is not None:

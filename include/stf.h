@@ -1,18 +1,23 @@
 /*
  * stf.h -- C ABI of the GB300 stochastic texture filtering library (libstf.so).
  *
- * The library performs batched filtered lookups into 2D MIP-mapped textures and
- * dense or sparse 3D voxel grids, following "Stochastic Texture Filtering"
- * (Fajardo, Wronski, Salvi, Pharr; arXiv 2305.05810):
+ * The library performs batched filtered lookups into 2D MIP-mapped textures (plain
+ * or DCT-compressed), dense or sparse 3D voxel grids and neural textures, following
+ * "Stochastic Texture Filtering" (Fajardo, Wronski, Salvi, Pharr; arXiv 2305.05810):
  *
  *   stochastic form   -- one tap per axis is drawn with probability |w| / sum|w|
  *                        from the separable filter weights (sampling arrays,
  *                        Section 2.2; Eq. 7-9 in Section 4) and the single texel
  *                        is returned, times sign(w) * sum|w| per axis for kernels
  *                        with negative lobes (Section 2.2, "Positivization", first
- *                        sentence).  Its expectation is the filtered value (Eq. 3).
- *   deterministic form -- the full weighted sum over 4 / 8 / 16 / 64 taps (Eq. 2,
- *                        Eq. 9), the same-GPU baseline.
+ *                        sentence), or two taps by positivization, or one texel by
+ *                        filter importance sampling (Section 4.4).  Its expectation
+ *                        is the filtered value (Eq. 3).
+ *   deterministic form -- the full weighted sum over every tap (Eq. 2, Eq. 9), the
+ *                        same-GPU baseline.
+ * Further entry points: anisotropic level of detail and EWA filtering, triplanar
+ * mapping, validation accumulators, neural-texture training, an allocation-free
+ * binned lookup.
  *
  * Conventions shared by every entry point:
  *   - Every call returns an stf_status.  On failure stf_last_error() returns a
@@ -31,7 +36,8 @@
  *     value outside the grid / outside active leaves.
  *   - Random variates: the i-th query of a call draws its variates from
  *     Philox4x32-10 with key = seed and counter = (q, q >> 32, sample_index, 0),
- *     q = query_offset + i (the positivized filter also uses counter word 3 = 1).
+ *     q = query_offset + i (counter word 3, the stream, is 0; the positivized filter
+ *     also draws stream 1, the cubic B-spline FIS filter streams 1 and 2).
  *     Results therefore do not depend on how a batch is
  *     split into calls, on launch shape, or on what else runs on the GPU.
  */

@@ -80,3 +80,24 @@ def test_request_over_budget_is_rejected_on_gpu(textures):
     big = serving.Request(0, "dense", torch.zeros((1 << 17, 3)))
     with pytest.raises(serving.BudgetError):
         sched.submit(big)
+
+
+def test_host_pipeline_equals_one_device_call():
+    """Chunked multi-stream lookups from pinned host memory return the results of one
+    device call over the whole batch (variates keyed by the global query index)."""
+    from paper_2305_05810_gb300.pipeline import HostPipeline
+    vals = synth.dense_density(n=64, seed=3, period=12.0)
+    T = stf.Texture(stf.KIND_DENSE3D, vals, dims=(64, 64, 64), fmt=stf.FMT_F16)
+    q = synth.camera_queries(W=200, H=100, steps=16, centre=(32, 32, 32), radius=96, half_span=56, seed=5)
+    n = q.shape[0]
+    whole = T.lookup(torch.from_numpy(q).cuda(), filter="bspline3", seed=9, query_offset=123)
+    h_q = torch.from_numpy(q).pin_memory()
+    h_out = torch.empty((n, 1), dtype=torch.float32).pin_memory()
+    pipe = HostPipeline(T, chunk=10007, n_streams=3)
+    pipe.lookup(stf.make_params("bspline3", seed=9, query_offset=123), h_q, h_out)
+    torch.cuda.synchronize()
+    assert torch.equal(whole.cpu(), h_out)
+    det = T.lookup_deterministic(torch.from_numpy(q).cuda(), filter="linear")
+    pipe.lookup(stf.make_params("linear"), h_q, h_out, stochastic=False)
+    torch.cuda.synchronize()
+    assert torch.equal(det.cpu(), h_out)
