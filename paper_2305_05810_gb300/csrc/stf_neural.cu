@@ -254,6 +254,17 @@ __device__ __forceinline__ uint64_t desc(const void* p, int K) {
   return d;
 }
 
+// The same with the 8-row-group stride set to 0: every group of 8 rows reads the same
+// two core matrices, so one 8-row tile stands for a 128-row operand whose rows are
+// all equal.
+__device__ __forceinline__ uint64_t desc_rows_repeated(const void* p) {
+  const uint32_t a = (uint32_t)__cvta_generic_to_shared(p);
+  uint64_t d = (uint64_t)((a & 0x3FFFF) >> 4);
+  d |= (uint64_t)(128 >> 4) << 16;
+  d |= (uint64_t)1 << 46;
+  return d;
+}
+
 // kind::f16 instruction descriptor: F32 accumulate, F16 A and B, both K-major.
 __host__ __device__ constexpr uint32_t idesc(int M, int N) {
   return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
@@ -315,19 +326,21 @@ struct Group {                       // one tile in flight
 };
 
 struct Smem {
-  unsigned char b1[B1_BYTES];
+  unsigned char b1[B1_BYTES];          // W1^T in k 0..7, (b1_hi, b1_lo) in k 8, 9
   unsigned char b2[B2_BYTES];
   unsigned char b3[B3_BYTES];
+  unsigned char b2x[64 * 16 * 2];      // (b2_hi, b2_lo) in k 0, 1
+  unsigned char b3x[16 * 16 * 2];      // (b3_hi, b3_lo) in k 0, 1
+  unsigned char ones[8 * 16 * 2];      // one 8-row group: 1 in columns 0, 1
   Group grp[2];
-  float bias[nn::NBIAS];
   uint32_t tmem;
 };
 
 }  // namespace tc
 
-// Hidden layer epilogue: D (64 float32 per row, tensor memory) + bias -> ReLU ->
-// binary16 row of the next A tile.
-__device__ __forceinline__ void tc_hidden(uint32_t taddr, const float* bias, unsigned char* a2, int row) {
+// Hidden layer epilogue: D (64 float32 per row, tensor memory, bias included by the
+// MMA) -> ReLU -> binary16 row of the next A tile.
+__device__ __forceinline__ void tc_hidden(uint32_t taddr, unsigned char* a2, int row) {
 #pragma unroll
   for (int half = 0; half < 2; ++half) {
     uint32_t r[32];
@@ -338,8 +351,8 @@ __device__ __forceinline__ void tc_hidden(uint32_t taddr, const float* bias, uns
 #pragma unroll
       for (int e = 0; e < 4; ++e) {
         const int c = 8 * q + 2 * e;
-        const float lo = __uint_as_float(r[c]) + bias[32 * half + c];
-        const float hi = __uint_as_float(r[c + 1]) + bias[32 * half + c + 1];
+        const float lo = __uint_as_float(r[c]);
+        const float hi = __uint_as_float(r[c + 1]);
         // ReLU and round to binary16 in one instruction (the first source goes to the
         // upper half)
         asm("cvt.rn.relu.f16x2.f32 %0, %1, %2;" : "=r"(w[e]) : "f"(hi), "f"(lo));
@@ -368,9 +381,28 @@ __global__ void __launch_bounds__(256, 4) k_neural_stochastic_tc(NeuralDev nd, L
   // weights: binary16 images -> K-major no-swizzle B tiles (16-byte rows)
   {
     const uint4* img = reinterpret_cast<const uint4*>(nd.wimg);
-    for (int e = tid; e < 64 * 2; e += 256) {        // W1^T: n < 64, k chunks of 8 (< 16)
-      const int n = e >> 1, kc = e & 1;
-      *reinterpret_cast<uint4*>(s.b1 + tc::off(n, 8 * kc, 16)) = __ldg(img + (nn::I_W1T + n * 24 + 8 * kc) / 8);
+    // Biases enter the MMAs as an extra K chunk: a bias b is split into binary16
+    // b_hi = fp16(b) and b_lo = fp16(b - b_hi), multiplied by two columns of ones, so
+    // the float32 accumulator receives b to about 2^-22 |b|.
+    auto split = [](float b) -> uint32_t {
+      const __half hi = __float2half_rn(b);
+      const __half lo = __float2half_rn(b - __half2float(hi));
+      return (uint32_t)__half_as_ushort(hi) | ((uint32_t)__half_as_ushort(lo) << 16);
+    };
+    for (int n = tid; n < 64; n += 256) {             // W1^T: n < 64, k 0..7; bias in k 8, 9
+      *reinterpret_cast<uint4*>(s.b1 + tc::off(n, 0, 16)) = __ldg(img + (nn::I_W1T + n * 24) / 8);
+      *reinterpret_cast<uint4*>(s.b1 + tc::off(n, 8, 16)) = make_uint4(split(__ldg(nd.bias + n)), 0, 0, 0);
+      *reinterpret_cast<uint4*>(s.b2x + tc::off(n, 0, 16)) = make_uint4(split(__ldg(nd.bias + 64 + n)), 0, 0, 0);
+      *reinterpret_cast<uint4*>(s.b2x + tc::off(n, 8, 16)) = make_uint4(0, 0, 0, 0);
+    }
+    for (int n = tid; n < 16; n += 256) {
+      const uint32_t b = n < 7 ? split(__ldg(nd.bias + 128 + n)) : 0u;
+      *reinterpret_cast<uint4*>(s.b3x + tc::off(n, 0, 16)) = make_uint4(b, 0, 0, 0);
+      *reinterpret_cast<uint4*>(s.b3x + tc::off(n, 8, 16)) = make_uint4(0, 0, 0, 0);
+    }
+    for (int r = tid; r < 8; r += 256) {
+      *reinterpret_cast<uint4*>(s.ones + tc::off(r, 0, 16)) = make_uint4(0x3C003C00u, 0, 0, 0);
+      *reinterpret_cast<uint4*>(s.ones + tc::off(r, 8, 16)) = make_uint4(0, 0, 0, 0);
     }
     for (int e = tid; e < 64 * 8; e += 256) {        // W2^T: n < 64, k chunks of 8 (< 64)
       const int n = e >> 3, kc = e & 7;
@@ -381,9 +413,9 @@ __global__ void __launch_bounds__(256, 4) k_neural_stochastic_tc(NeuralDev nd, L
       *reinterpret_cast<uint4*>(s.b3 + tc::off(n, 8 * kc, 64)) =
           n < 8 ? __ldg(img + (nn::I_W3T + n * 72 + 8 * kc) / 8) : make_uint4(0, 0, 0, 0);
     }
-    for (int k = tid; k < nn::NBIAS; k += 256) s.bias[k] = __ldg(nd.bias + k);
-    // latent columns 8..15 of A1 stay zero
-    *reinterpret_cast<uint4*>(G.a1 + tc::off(row, 8, 16)) = make_uint4(0, 0, 0, 0);
+    // columns 8..15 of A1: the ones that multiply W1's bias rows, then zeros (the
+    // gathers write columns 0..7 only)
+    *reinterpret_cast<uint4*>(G.a1 + tc::off(row, 8, 16)) = make_uint4(0x3C003C00u, 0, 0, 0);
   }
   if (row == 0) {
     G.abort = 0;
@@ -431,7 +463,7 @@ __global__ void __launch_bounds__(256, 4) k_neural_stochastic_tc(NeuralDev nd, L
     NeuralPick nxt;
     if (next < ntiles) nxt = neural_pick<F>(nd, a, next * tc::ROWS + row, arow);
     cp_async_commit();
-    tc_hidden(trow, s.bias, G.a2, row);
+    tc_hidden(trow, G.a2, row);
     asm volatile("fence.proxy.async.shared::cta;");
     asm volatile("tcgen05.fence::before_thread_sync;");
     group_sync(g);
@@ -441,6 +473,7 @@ __global__ void __launch_bounds__(256, 4) k_neural_stochastic_tc(NeuralDev nd, L
 #pragma unroll
       for (int kk = 0; kk < 4; ++kk)
         tc::mma(tmem, tc::desc(G.a2 + kk * 256, 64), tc::desc(s.b2 + kk * 256, 64), tc::idesc(128, 64), kk);
+      tc::mma(tmem, tc::desc_rows_repeated(s.ones), tc::desc(s.b2x, 16), tc::idesc(128, 64), 1);   // + b2
       tc::commit(&G.bar);
       if (!tc::wait_bar(&G.bar, parity)) G.abort = 1;
     }
@@ -448,7 +481,7 @@ __global__ void __launch_bounds__(256, 4) k_neural_stochastic_tc(NeuralDev nd, L
     group_sync(g);
     if (G.abort) break;
     asm volatile("tcgen05.fence::after_thread_sync;");
-    tc_hidden(trow, s.bias + 64, G.a2, row);
+    tc_hidden(trow, G.a2, row);
     asm volatile("fence.proxy.async.shared::cta;");
     asm volatile("tcgen05.fence::before_thread_sync;");
     group_sync(g);
@@ -458,6 +491,7 @@ __global__ void __launch_bounds__(256, 4) k_neural_stochastic_tc(NeuralDev nd, L
 #pragma unroll
       for (int kk = 0; kk < 4; ++kk)
         tc::mma(tmem, tc::desc(G.a2 + kk * 256, 64), tc::desc(s.b3 + kk * 256, 64), tc::idesc(128, 16), kk);
+      tc::mma(tmem, tc::desc_rows_repeated(s.ones), tc::desc(s.b3x, 16), tc::idesc(128, 16), 1);   // + b3
       tc::commit(&G.bar);
       if (!tc::wait_bar(&G.bar, parity)) G.abort = 1;
     }
@@ -470,7 +504,7 @@ __global__ void __launch_bounds__(256, 4) k_neural_stochastic_tc(NeuralDev nd, L
       uint32_t r[8];
       tc::tmem_ld<8>(trow, r);
 #pragma unroll
-      for (int k = 0; k < 7; ++k) v[k] = __uint_as_float(r[k]) + s.bias[128 + k];
+      for (int k = 0; k < 7; ++k) v[k] = __uint_as_float(r[k]);
     }
     if (cur.mode == 2) {
       const uint32_t* tw = reinterpret_cast<const uint32_t*>(&fb);
