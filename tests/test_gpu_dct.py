@@ -189,3 +189,32 @@ def test_ewa_on_dct_texture():
     assert np.all(same | ex)
     err = np.abs(out.cpu().numpy().astype(np.float64) - rv)[same]
     assert np.all(err <= 2.5 * _decode_tol(ref)), np.max(err)
+
+
+def test_dct_edge_blocks_of_non_multiple_of_8_sizes():
+    """A 60x44 single-level DCT texture: the partial blocks on the right and bottom
+    edges decode like the oracle's (edge texels repeated into the block)."""
+    base = synth.texture2d(64, 64, 4, seed=31)[:44, :60].copy()
+    T = stf.Texture(stf.KIND_TEX2D, base, dims=(60, 44, 1), channels=4, fmt=stf.FMT_DCT6)
+    ref = dct.DCTTexture2D([base.astype(np.float64)])
+    ys, xs = np.mgrid[0:44, 0:60]
+    uv = np.stack([(xs.ravel() + 0.5) / 60, (ys.ravel() + 0.5) / 44], axis=1).astype(np.float32)
+    out = T.lookup(to_dev(uv), filter="fis_linear", seed=2)
+    want = ref.fetch(0, xs.ravel(), ys.ravel())
+    ok = ~ref.exempt_texels(0, xs.ravel(), ys.ravel())
+    err = np.abs(out.cpu().numpy().astype(np.float64) - want)[ok]
+    assert np.all(err <= _decode_tol(ref)), np.max(err)
+
+
+def test_triplanar_scale_and_no_lod():
+    lv = _pyramid(32, 32, 2, 1, 33)
+    T = stf.Texture(stf.KIND_TEX2D, lv[0], dims=(32, 32, 1), channels=2)
+    ref = textures.Texture2D([lv[0].astype(np.float64)])
+    p, nrm = _tri_queries(5000, 34)
+    taps = torch.empty((p.shape[0], 4), dtype=torch.int32, device=dev())
+    out = T.lookup_triplanar(to_dev(p), to_dev(nrm), 0.75, None, taps=taps, filter="bspline3", seed=8)
+    rv, rt, ex = dct.lookup_triplanar(ref, p, nrm, 0.75, None, "bspline3", stochastic_form=True, seed=8)
+    torch.cuda.synchronize()
+    same = np.all(taps.cpu().numpy() == rt, axis=1)
+    assert np.all(same | ex)
+    assert np.array_equal(out.cpu().numpy().astype(np.float64)[same], rv[same])

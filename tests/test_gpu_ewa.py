@@ -172,3 +172,24 @@ def test_ewa_argument_checks():
     assert e.value.status == 4
     stf.stf_lookup_batch_ewa(T.handle, p, uv, g, 0, 8.0, out)      # n = 0: no-op
     torch.cuda.synchronize()
+
+
+def test_ewa_single_level_texture():
+    """Without a pyramid every lookup filters level 0 (lod clamped), in both forms."""
+    base = synth.texture2d(32, 32, 1, seed=41)
+    T = stf.Texture(stf.KIND_TEX2D, base, dims=(32, 32, 1), channels=1)
+    ref = textures.Texture2D([base.astype(np.float64)])
+    uv, g = _queries(1500, 32, 12)
+    n = uv.shape[0]
+    taps = torch.empty((n, 4), dtype=torch.int32, device=dev())
+    out = T.lookup_ewa(to_dev(uv), to_dev(g), 8.0, taps=taps, seed=3)
+    rv, rt, ex = ewa.lookup(ref, uv, g, 8.0, stochastic_form=True, seed=3)
+    torch.cuda.synchronize()
+    gt = taps.cpu().numpy()
+    assert np.all(gt[gt[:, 3] >= 0, 3] == 0)
+    same = np.all(gt == rt, axis=1)
+    assert np.all(same | ex) and not np.any(ex)
+    assert np.array_equal(out.cpu().numpy().astype(np.float64)[same], rv[same])
+    det = T.lookup_ewa_deterministic(to_dev(uv), to_dev(g), 8.0)
+    dv, _, _ = ewa.lookup(ref, uv, g, 8.0, stochastic_form=False)
+    assert np.allclose(det.cpu().numpy(), dv, atol=2e-5)

@@ -254,3 +254,16 @@ def test_full_size_dense_fis_bspline3_sampled():
     rv, rt, ex = filters.lookup_3d(ref, q[idx], "fis_bspline3", stochastic_form=True, seed=2024,
                                    qid=idx.astype(np.uint64))
     _check_fis("fis_bspline3", out.cpu().numpy()[idx], taps.cpu().numpy()[idx], rv, rt, ex)
+
+
+def test_fis_ignores_reuse_flag():
+    """reuse_xi has no meaning for FIS (and positivization): results are the same."""
+    vals = synth.dense_density(n=32, seed=3, period=8.0)
+    T = stf.Texture(stf.KIND_DENSE3D, vals, dims=(32, 32, 32), fmt=stf.FMT_F16)
+    q = to_dev(synth.uniform(3 * 20000, 9).reshape(-1, 3) * np.float32(30))
+    for filt in ("fis_linear", "fis_bspline3", "fis_gaussian", "catmull_rom_positivized"):
+        w = 0.7 if filt == "fis_gaussian" else 0.0
+        a = T.lookup(q, filter=filt, seed=4, width=w)
+        b = T.lookup(q, filter=filt, seed=4, width=w, reuse_xi=True)
+        torch.cuda.synchronize()
+        assert torch.equal(a, b), filt
