@@ -736,17 +736,22 @@ def run_ours(args):
                 extras[name] = {"unavailable": str(e)}
         if w["name"] == "sparse_e4m3":
             # storage error: deterministic tricubic on E4M3 leaves against the same lookups on
-            # the FP32 leaves (first 2^20 queries), in units of the voxel values' range
+            # the FP32 leaves, over every 64th query (all of the image), in units of the
+            # voxel values; rms over the lookups that touch the cloud (non-zero FP32 value)
             f32 = stf.Texture(stf.KIND_SPARSE3D, w["values"], fmt=stf.FMT_F32, leaf_origins=w["origins"])
-            m = 1 << 20
+            sub = coords[::64].contiguous()
+            m = sub.shape[0]
             ref32 = torch.empty((m, 1), dtype=torch.float32, device=dev)
+            got = torch.empty((m, 1), dtype=torch.float32, device=dev)
             pq = stf.make_params(filt)
-            stf.stf_lookup_batch_deterministic(f32.handle, pq, coords, None, m, ref32, stream)
-            stf.stf_lookup_batch_deterministic(tex.handle, pq, coords, None, m, out, stream)
-            err = (out[:m] - ref32).abs()
+            stf.stf_lookup_batch_deterministic(f32.handle, pq, sub, None, m, ref32, stream)
+            stf.stf_lookup_batch_deterministic(tex.handle, pq, sub, None, m, got, stream)
+            err = (got - ref32).abs()
+            hit = ref32 != 0
             rng = float(w["values"].max() - w["values"].min())
-            extras["e4m3_error_vs_fp32_leaves"] = {"max_abs": float(err.max()), "rms": float(err.pow(2).mean().sqrt()),
-                                                   "value_range": rng, "queries": m}
+            extras["e4m3_error_vs_fp32_leaves"] = {
+                "max_abs": float(err.max()), "rms_in_cloud": float(err[hit].pow(2).mean().sqrt()),
+                "lookups_in_cloud": int(hit.sum()), "value_range": rng, "queries": m}
             f32.close()
         if w["name"] == "tex2d":
             # the 65,536-query configuration: per-launch latency over 1000 launches, and the

@@ -8,6 +8,7 @@
 // no layout; this one keeps the NanoVDB fan-outs and voxel order
 // (x & 7) << 6 | (y & 7) << 3 | (z & 7) within a leaf.
 #include <algorithm>
+#include <climits>
 #include <vector>
 
 #include "stf_internal.h"
@@ -109,7 +110,6 @@ stf_status build_sparse(stf_texture_s* t, const stf_texture_desc* d, cudaStream_
   std::vector<uint32_t> uprefix((size_t)n_upper * 512, 0);
   std::vector<int32_t> ubase((size_t)n_upper, 0), uorigin((size_t)n_upper * 3);
   std::vector<uint64_t> lmask;
-  std::vector<uint32_t> lprefix;
   std::vector<int32_t> lbase, perm((size_t)nl);
   int64_t prev_lower_key = -1;
   int prev_upper = -1;
@@ -127,13 +127,14 @@ stf_status build_sparse(stf_texture_s* t, const stf_texture_desc* d, cudaStream_
       umask[(size_t)u * 512 + (lb >> 6)] |= 1ull << (lb & 63);
       lbase.push_back((int32_t)l);
       lmask.resize(lmask.size() + 64, 0);
-      lprefix.resize(lprefix.size() + 64, 0);
     }
     lmask[(lbase.size() - 1) * 64 + (fb >> 6)] |= 1ull << (fb & 63);
   }
   const int n_lower = (int)lbase.size();
+  // Absolute prefixes: the node or leaf index of each word's first set bit, so a
+  // lookup adds only the popcount below its bit.
   for (int u = 0; u < n_upper; ++u) {
-    uint32_t acc = 0;
+    uint32_t acc = (uint32_t)ubase[u];
     for (int w = 0; w < 512; ++w) {
       uprefix[(size_t)u * 512 + w] = acc;
       acc += (uint32_t)__builtin_popcountll(umask[(size_t)u * 512 + w]);
@@ -142,25 +143,27 @@ stf_status build_sparse(stf_texture_s* t, const stf_texture_desc* d, cudaStream_
     uorigin[3 * u + 1] = uppers[u].y;
     uorigin[3 * u + 2] = uppers[u].z;
   }
+  std::vector<uint32_t> lrec((size_t)n_lower * 64 * 4, 0);
   for (int lo = 0; lo < n_lower; ++lo) {
-    uint32_t acc = 0;
+    uint32_t acc = (uint32_t)lbase[lo];
     for (int w = 0; w < 64; ++w) {
-      lprefix[(size_t)lo * 64 + w] = acc;
-      acc += (uint32_t)__builtin_popcountll(lmask[(size_t)lo * 64 + w]);
+      const uint64_t m = lmask[(size_t)lo * 64 + w];
+      uint32_t* r = lrec.data() + ((size_t)lo * 64 + w) * 4;
+      r[0] = (uint32_t)m;
+      r[1] = (uint32_t)(m >> 32);
+      r[2] = acc;
+      acc += (uint32_t)__builtin_popcountll(m);
     }
   }
   // One device allocation: nodes, then leaves.
   const size_t b_uo = align256(sizeof(int32_t) * 3 * (size_t)std::max(n_upper, 1));
   const size_t b_um = align256(sizeof(uint64_t) * umask.size() + 8);
   const size_t b_up = align256(sizeof(uint32_t) * uprefix.size() + 4);
-  const size_t b_ub = align256(sizeof(int32_t) * ubase.size() + 4);
-  const size_t b_lm = align256(sizeof(uint64_t) * lmask.size() + 8);
-  const size_t b_lp = align256(sizeof(uint32_t) * lprefix.size() + 4);
-  const size_t b_lb = align256(sizeof(int32_t) * lbase.size() + 4);
+  const size_t b_lr = align256(sizeof(uint32_t) * lrec.size() + 16);
   const bool e4 = d->format == STF_FMT_E4M3_SCALED;
   const size_t b_leaf = align256((size_t)nl * 512 * (e4 ? 1 : 4) + 16);
   const size_t b_scale = e4 ? align256(sizeof(float) * (size_t)nl + 4) : 0;
-  const size_t total = b_uo + b_um + b_up + b_ub + b_lm + b_lp + b_lb + b_leaf + b_scale;
+  const size_t total = b_uo + b_um + b_up + b_lr + b_leaf + b_scale;
   e = dev_alloc(&t->d_tree, total);
   if (e != cudaSuccess) return fail_cuda(e, "sparse tree allocation");
   t->bytes += (int64_t)total;
@@ -173,10 +176,7 @@ stf_status build_sparse(stf_texture_s* t, const stf_texture_desc* d, cudaStream_
   g.upper_origin = (const int32_t*)p;     p += b_uo;
   g.upper_mask = (const uint64_t*)p;      p += b_um;
   g.upper_prefix = (const uint32_t*)p;    p += b_up;
-  g.upper_lower_base = (const int32_t*)p; p += b_ub;
-  g.lower_mask = (const uint64_t*)p;      p += b_lm;
-  g.lower_prefix = (const uint32_t*)p;    p += b_lp;
-  g.lower_leaf_base = (const int32_t*)p;  p += b_lb;
+  g.lower_rec = (const uint4*)p;          p += b_lr;
   if (e4) {
     g.leaf_e4m3 = (const uint8_t*)p;      p += b_leaf;
     g.leaf_scale = (const float*)p;       p += b_scale;
@@ -187,10 +187,7 @@ stf_status build_sparse(stf_texture_s* t, const stf_texture_desc* d, cudaStream_
       {g.upper_origin, uorigin.data(), sizeof(int32_t) * uorigin.size()},
       {g.upper_mask, umask.data(), sizeof(uint64_t) * umask.size()},
       {g.upper_prefix, uprefix.data(), sizeof(uint32_t) * uprefix.size()},
-      {g.upper_lower_base, ubase.data(), sizeof(int32_t) * ubase.size()},
-      {g.lower_mask, lmask.data(), sizeof(uint64_t) * lmask.size()},
-      {g.lower_prefix, lprefix.data(), sizeof(uint32_t) * lprefix.size()},
-      {g.lower_leaf_base, lbase.data(), sizeof(int32_t) * lbase.size()}};
+      {g.lower_rec, lrec.data(), sizeof(uint32_t) * lrec.size()}};
   for (const Up& u : ups)
     if (u.bytes && e == cudaSuccess) e = cudaMemcpy((void*)u.dst, u.src, u.bytes, cudaMemcpyHostToDevice);
   if (e != cudaSuccess) return fail_cuda(e, "sparse tree upload");
@@ -224,19 +221,24 @@ stf_status build_sparse(stf_texture_s* t, const stf_texture_desc* d, cudaStream_
 struct UpperSmem {
   uint64_t mask[512];
   uint32_t prefix[512];
+  int32_t origin[3];       // upper node 0 (origin[0] = INT_MIN without upper nodes)
 };
 
 // Leaf index holding voxel (x, y, z), or -1 if the voxel lies in no active leaf.
-// Upper node 0 is read from shared memory.
+// Upper node 0 (origin, mask and prefixes) is read from shared memory.
 __device__ __forceinline__ int64_t sparse_leaf(const SparseDev& g, const UpperSmem& su, int x,
                                                int y, int z) {
   const int ox = x & ~4095, oy = y & ~4095, oz = z & ~4095;
   int u = -1;
-  for (int j = 0; j < g.n_upper; ++j) {
-    const int32_t* o = g.upper_origin + 3 * j;
-    if (__ldg(o) == ox && __ldg(o + 1) == oy && __ldg(o + 2) == oz) {
-      u = j;
-      break;
+  if (su.origin[0] == ox && su.origin[1] == oy && su.origin[2] == oz) {
+    u = 0;
+  } else {
+    for (int j = 1; j < g.n_upper; ++j) {
+      const int32_t* o = g.upper_origin + 3 * j;
+      if (__ldg(o) == ox && __ldg(o + 1) == oy && __ldg(o + 2) == oz) {
+        u = j;
+        break;
+      }
     }
   }
   if (u < 0) return -1;
@@ -252,17 +254,17 @@ __device__ __forceinline__ int64_t sparse_leaf(const SparseDev& g, const UpperSm
     pre = __ldg(g.upper_prefix + (int64_t)u * 512 + (lb >> 6));
   }
   if (!(m & bit)) return -1;
-  const int lower = __ldg(g.upper_lower_base + u) + (int)pre + __popcll(m & (bit - 1));
+  const int lower = (int)pre + __popcll(m & (bit - 1));
   if ((unsigned)lower >= (unsigned)g.n_lower) {
     atomicOr(g.status, STF_DEV_BAD_NODE);
     return -1;
   }
   const int fb = (((x >> 3) & 15) << 8) | (((y >> 3) & 15) << 4) | ((z >> 3) & 15);
   const uint64_t bit2 = 1ull << (fb & 63);
-  const uint64_t m2 = __ldg(g.lower_mask + (int64_t)lower * 64 + (fb >> 6));
+  const uint4 rec = __ldg(g.lower_rec + (int64_t)lower * 64 + (fb >> 6));
+  const uint64_t m2 = (uint64_t)rec.x | ((uint64_t)rec.y << 32);
   if (!(m2 & bit2)) return -1;
-  const int64_t leaf = (int64_t)__ldg(g.lower_leaf_base + lower) +
-                       __ldg(g.lower_prefix + (int64_t)lower * 64 + (fb >> 6)) + __popcll(m2 & (bit2 - 1));
+  const int64_t leaf = (int64_t)rec.z + __popcll(m2 & (bit2 - 1));
   if (leaf >= g.n_leaves) {
     atomicOr(g.status, STF_DEV_BAD_NODE);
     return -1;
@@ -290,6 +292,7 @@ __device__ __forceinline__ void stage_upper(const SparseDev& g, UpperSmem& su) {
       su.prefix[k] = __ldg(g.upper_prefix + k);
     }
   }
+  if (threadIdx.x < 3) su.origin[threadIdx.x] = g.n_upper > 0 ? __ldg(g.upper_origin + threadIdx.x) : INT_MIN;
   __syncthreads();
 }
 

@@ -19,13 +19,12 @@ struct SparseDev {
   int32_t n_upper;
   const int32_t* upper_origin;     // n_upper x 3
   const uint64_t* upper_mask;      // n_upper x 512 words (32^3 child bits)
-  const uint32_t* upper_prefix;    // n_upper x 512: set bits before each word
-  const int32_t* upper_lower_base; // n_upper: index of the node's first lower node
-  // Lower nodes (each covers 128^3 voxels, 16^3 leaves).
+  const uint32_t* upper_prefix;    // n_upper x 512: index of the lower node of the first
+                                   // set bit of each word (node base + set bits before it)
+  // Lower nodes (each covers 128^3 voxels, 16^3 leaves): one 16-byte record per mask
+  // word, {mask low, mask high, index of the leaf of the word's first set bit, 0}.
   int32_t n_lower;
-  const uint64_t* lower_mask;      // n_lower x 64 words
-  const uint32_t* lower_prefix;    // n_lower x 64
-  const int32_t* lower_leaf_base;  // n_lower
+  const uint4* lower_rec;          // n_lower x 64
   // Leaves: 512 values each, [x&7][y&7][z&7].
   int64_t n_leaves;
   const float* leaf_f32;           // FP32 format
