@@ -10,7 +10,14 @@ scale and store).  The same-GPU deterministic 64-tap filter, the trilinear pair 
 the Morton-binned variant are timed beside it and reported in extra keys.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
-                    [--workload dense|tex2d|sparse]
+                    [--workload dense|tex2d|sparse|sparse_e4m3|neural|serving|aniso|dct]
+
+Other workloads: a 2D RGBA texture, the sparse 2048^3 cloud (FP32 or E4M3 leaves), the
+neural texture, a continuous-batching serving mix, anisotropic EWA filtering of a ground
+plane, and a DCT-compressed texture set with triplanar mapping.  Every line carries the
+same-GPU deterministic filter in `extras`, an end-to-end figure through the C ABI from
+pinned host buffers (`e2e`), the oracle's CPU rate (`cpu_baseline`) and the roofline of the
+timed kernel.
 
 Timing: CUDA events on the launching stream, W untimed warm-up steps, barrier and
 synchronize on both sides of K timed steps, max over ranks.  The query and output
