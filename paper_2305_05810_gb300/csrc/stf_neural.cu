@@ -282,14 +282,17 @@ __device__ __forceinline__ void commit(uint64_t* bar) {
       (uint32_t)__cvta_generic_to_shared(bar)));
 }
 
-// Wait for phase `parity` of the mbarrier, at most ~2^22 polls; false on timeout.
+// Wait for phase `parity` of the mbarrier; false on timeout.  Each try_wait may suspend
+// the thread for up to 20 us, waking it when the phase completes, so the waiting lane
+// does not spin on the issue slots its warp shares with the computing warps; at most
+// 2^16 tries (about 1.3 s).
 __device__ __forceinline__ bool wait_bar(uint64_t* bar, uint32_t parity) {
   const uint32_t a = (uint32_t)__cvta_generic_to_shared(bar);
   uint32_t done = 0;
-  for (int it = 0; it < (1 << 22) && !done; ++it) {
+  for (int it = 0; it < (1 << 16) && !done; ++it) {
     asm volatile(
-        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(done) : "r"(a), "r"(parity));
+        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\nselp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done) : "r"(a), "r"(parity), "r"(20000u));
   }
   return done != 0;
 }
