@@ -165,3 +165,41 @@ def test_training_gains_over_untrained_decoder():
     a = T.lookup_deterministic(uv, filter="linear").cpu().numpy()
     b = stored.lookup_deterministic(uv, filter="linear").cpu().numpy()[:, :7]
     assert np.sqrt(np.mean((a - b) ** 2)) < 0.25 * np.sqrt(l0 / 7)
+
+
+def test_full_size_neural_sampled():
+    """The benchmark's neural workload (4096^2, four 8-channel FP16 latent levels, FP16
+    fallback mips, 16,777,216 uv with lod ~ U[0, 4), nearest level, bilinear tap) in the
+    benchmark's launch configuration, with the untrained decoder; outputs checked on a
+    seeded sample of 2^14 queries against the oracle's decode."""
+    size, nlat, nlev = 4096, 4, 13
+    lat, par = synth.neural_init(size, nlat, seed=5)
+    pyr = synth.box_levels(synth.material(size, seed=5), nlev)
+    fb = np.concatenate([p.reshape(-1, 7) for p in pyr[nlat:]])
+    T = stf.NeuralTexture(size, size, nlat, nlev, lat, par, fb)
+    n = 1 << 24
+    uv = synth.uv_queries(n, seed=2)
+    lod = synth.lods(n, seed=9)
+    taps = torch.empty((n, 4), dtype=torch.int32, device=dev())
+    out = T.lookup(to_dev(uv), to_dev(lod), taps=taps, filter="linear", seed=2024,
+                   level_mode=stf.LEVEL_NEAREST)
+    torch.cuda.synchronize()
+    idx = np.sort(np.random.default_rng(3).choice(n, 1 << 14, replace=False))
+    ref = neural.NeuralTexture2D(split_levels(h16(lat), size, 0, nlat, 8), stored_params(par),
+                                 [h16(p) for p in pyr[nlat:]])
+    rv, rt, ex = filters.lookup_2d(ref, uv[idx], lod[idx], "linear", stochastic_form=True, seed=2024,
+                                   level_mode=stf.LEVEL_NEAREST, qid=idx.astype(np.uint64))
+    g_taps = taps.cpu().numpy()[idx]
+    g_out = out.cpu().numpy()[idx].astype(np.float64)
+    same = np.all(g_taps == rt, axis=1)
+    assert np.all(same | ex)
+    lvl = rt[:, 3]
+    bound = np.full(rv.shape, 1e-6)
+    dec = same & (lvl >= 0) & (lvl < nlat)
+    for L in np.unique(lvl[dec]):
+        m = dec & (lvl == L)
+        w, h = ref.size(L)
+        Z = ref.latents[L][np.clip(rt[m, 1], 0, h - 1), np.clip(rt[m, 0], 0, w - 1)]
+        bound[m] = decode_bound(Z, ref.P)
+    err = np.abs(g_out - rv)
+    assert np.all(err[same] <= bound[same] + 2e-6 * np.abs(rv[same])), np.max(err[same] - bound[same])
