@@ -46,6 +46,9 @@ template <> struct Filter<STF_FILTER_LINEAR> {
     w[1] = f;
   }
   __device__ __forceinline__ static void cdf(float f, float* c) { c[0] = 1.0f - f; }
+  // The same boundary times 2^24, for comparison with the 24-bit integer variate:
+  // a power-of-two scale, so every rounding is the scaled one and the choice is equal.
+  __device__ __forceinline__ static void cdf24(float f, float* c) { c[0] = fmaf(f, -16777216.0f, 16777216.0f); }
 };
 
 // Cubic B-spline K_bs (Appendix A, "Convolutional"): with g = 1 - f the four taps
@@ -67,6 +70,13 @@ template <> struct Filter<STF_FILTER_BSPLINE3> {
     c[0] = g * g * (g * (1.0f / 6.0f));
     c[1] = fmaf(fmaf(fmaf(f, 1.0f / 3.0f, -0.5f), f, -0.5f), f, 5.0f / 6.0f);
     c[2] = fmaf(f2, f * (-1.0f / 6.0f), 1.0f);
+  }
+  // cdf() times 2^24 (every constant scaled by the power of two: the same roundings).
+  __device__ __forceinline__ static void cdf24(float f, float* c) {
+    const float g = 1.0f - f, f2 = f * f;
+    c[0] = g * g * (g * (16777216.0f / 6.0f));
+    c[1] = fmaf(fmaf(fmaf(f, 16777216.0f / 3.0f, -8388608.0f), f, -8388608.0f), f, 16777216.0f * 5.0f / 6.0f);
+    c[2] = fmaf(f2, f * (-16777216.0f / 6.0f), 16777216.0f);
   }
 };
 
@@ -199,6 +209,35 @@ __device__ __forceinline__ float pick_taps(const float* x, const float* u, int* 
     idx[a] = b + Fl::OFF0 + p.k;
   }
   return sigma;
+}
+
+// pick_taps from the raw Philox words r (word a for axis a).  For the closed-form
+// kernels the 24-bit integer variate is compared with the boundaries scaled by 2^24,
+// which skips the conversion of the variate to [0, 1) and decides identically.
+template <int F, int D, bool REUSE>
+__device__ __forceinline__ float pick_taps_r(const float* x, const uint4& r, int* idx) {
+  using Fl = Filter<F>;
+  const uint32_t w[4] = {r.x, r.y, r.z, r.w};
+  if constexpr (!REUSE && Fl::UNIT_SUM) {
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+      float f;
+      const int b = axis_base(x[a], f);
+      float c[Fl::T - 1];
+      Fl::cdf24(f, c);
+      const float R = (float)(w[a] >> 8);
+      int k = 0;
+#pragma unroll
+      for (int j = 0; j < Fl::T - 1; ++j) k += (R >= c[j]) ? 1 : 0;
+      idx[a] = b + Fl::OFF0 + k;
+    }
+    return 1.0f;
+  } else {
+    float u[D];
+#pragma unroll
+    for (int a = 0; a < D; ++a) u[a] = unit24(w[a]);
+    return pick_taps<F, D, REUSE>(x, u, idx);
+  }
 }
 
 // ---------------------------------------------------------------- views

@@ -52,9 +52,8 @@ __device__ __forceinline__ float dense_stochastic_one(const Dense3DView& g, cons
     if (Wn > 0.0f) t = fmaf(-Wn, dense_fetch<FMT>(g, in[0], in[1], in[2]), t);
     return t;
   } else {
-    const float u[3] = {unit24(r.x), unit24(r.y), unit24(r.z)};
     int idx[3];
-    const float sigma = pick_taps<F, 3, REUSE>(x, u, idx);
+    const float sigma = pick_taps_r<F, 3, REUSE>(x, r, idx);
     tap = make_int4(idx[0], idx[1], idx[2], 0);
     float t = dense_fetch<FMT>(g, idx[0], idx[1], idx[2]);
     if constexpr (!Filter<F>::NONNEG) t *= sigma;

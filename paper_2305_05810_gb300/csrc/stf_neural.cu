@@ -211,9 +211,8 @@ __device__ __forceinline__ NeuralPick neural_pick(const NeuralDev& nd, const Loo
   const int w = nd.lvl_w[L], h = nd.lvl_h[L];
   float x[2] = {__fsub_rn(__fmul_rn(uv.x, (float)w), 0.5f), __fsub_rn(__fmul_rn(uv.y, (float)h), 0.5f)};
   if (!(prepare_coords<2>(x) && isfinite(lod))) return pk;
-  const float u[2] = {unit24(r.x), unit24(r.y)};
   int idx[2];
-  pk.sigma = pick_taps<F, 2, false>(x, u, idx);
+  pk.sigma = pick_taps_r<F, 2, false>(x, r, idx);
   pk.tap = make_int4(idx[0], idx[1], 0, L);
   const int cx = min(max(idx[0], 0), w - 1), cy = min(max(idx[1], 0), h - 1);
   const __half* base = L < nd.nlat ? nd.lat16 : nd.fb16;

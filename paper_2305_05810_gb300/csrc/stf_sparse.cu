@@ -324,9 +324,8 @@ __device__ __forceinline__ float sparse_stochastic_one(const SparseDev& g, const
       t = fmaf(-Wn, sparse_value<FMT>(g, sparse_leaf(g, su, in[0], in[1], in[2]), in[0], in[1], in[2]), t);
     return t;
   } else {
-    const float u[3] = {unit24(r.x), unit24(r.y), unit24(r.z)};
     int idx[3];
-    const float sigma = pick_taps<F, 3, REUSE>(x, u, idx);
+    const float sigma = pick_taps_r<F, 3, REUSE>(x, r, idx);
     tap = make_int4(idx[0], idx[1], idx[2], 0);
     float t = sparse_value<FMT>(g, sparse_leaf(g, su, idx[0], idx[1], idx[2]), idx[0], idx[1], idx[2]);
     if constexpr (!Filter<F>::NONNEG) t *= sigma;

@@ -72,9 +72,8 @@ __device__ __forceinline__ void tex2d_stochastic_at(const Tex2DView& t, const Lo
       for (int c = 0; c < C; ++c) v[c] = fmaf(-Wn, tn[c], v[c]);
     }
   } else {
-    const float u[2] = {unit24(r.x), unit24(r.y)};
     int idx[2];
-    const float sigma = pick_taps<F, 2, REUSE>(x, u, idx);
+    const float sigma = pick_taps_r<F, 2, REUSE>(x, r, idx);
     tap = make_int4(idx[0], idx[1], 0, L);
     fetch_clamped<FMT, C>(t, L, idx[0], idx[1], v);
     if constexpr (!Filter<F>::NONNEG) {
