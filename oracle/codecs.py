@@ -17,6 +17,7 @@ import numpy as np
 
 
 def e4m3_decode(code):
+    """Exact value of each OCP E4M3 code (bias 7, no infinities, 0x7F/0xFF NaN)."""
     c = np.asarray(code, dtype=np.int64) & 0xFF
     s = np.where(c >> 7, -1.0, 1.0)
     e = (c >> 3) & 0xF
@@ -27,6 +28,7 @@ def e4m3_decode(code):
 
 
 def f16_decode(code):
+    """Exact value of each IEEE binary16 code."""
     c = np.asarray(code, dtype=np.int64) & 0xFFFF
     s = np.where(c >> 15, -1.0, 1.0)
     e = (c >> 10) & 0x1F

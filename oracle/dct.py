@@ -149,6 +149,7 @@ class DCTTexture2D:
         self.c = basis_1d()
 
     def size(self, level):
+        """(width, height) of a level."""
         return self.sizes[level]
 
     def fetch(self, level, ix, iy):

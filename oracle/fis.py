@@ -96,6 +96,7 @@ def gaussian_nearest(x32, off):
 
 
 def gaussian_reach(sigma):
+    """Largest offset of a 24-bit Box-Muller draw: 5.77 sigma."""
     return GAUSS_REACH * sigma
 
 

@@ -16,17 +16,21 @@ import numpy as np
 
 
 def k0_box(t):
+    """Unit box K0 (Appendix A): 1 on |t| < 1/2, else 0."""
     t = np.asarray(t)
     return np.where(np.abs(t) < 0.5, t.dtype.type(1), t.dtype.type(0))
 
 
 def k1_tent(t):
+    """Unit tent K1 (Appendix A): 1 - |t| on |t| < 1, else 0."""
     t = np.asarray(t)
     a = np.abs(t)
     return np.where(a < 1, 1 - a, t.dtype.type(0))
 
 
 def k3_cubic(t, a=-0.5):
+    """Cubic K3 (Appendix A): (a+2)|t|^3 - (a+3)|t|^2 + 1 on |t| <= 1,
+    a|t|^3 - 5a|t|^2 + 8a|t| - 4a on 1 < |t| < 2, else 0."""
     t = np.asarray(t)
     x = np.abs(t)
     a = t.dtype.type(a)
@@ -36,6 +40,8 @@ def k3_cubic(t, a=-0.5):
 
 
 def k_bspline3(t):
+    """Cubic B-spline K_bs (Appendix A, "Convolutional"): (4 - 6|t|^2 + 3|t|^3)/6
+    on |t| <= 1, (2 - |t|)^3 / 6 on 1 < |t| <= 2, else 0."""
     t = np.asarray(t)
     x = np.abs(t)
     sixth = t.dtype.type(1) / 6

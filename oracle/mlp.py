@@ -20,6 +20,7 @@ NAMES = ("W1", "b1", "W2", "b2", "W3", "b3")
 
 
 def shapes(din=8, hidden=64, dout=7):
+    """Parameter shapes of the decoder (W1, b1, W2, b2, W3, b3), in flattening order."""
     return {"W1": (din, hidden), "b1": (hidden,), "W2": (hidden, hidden), "b2": (hidden,),
             "W3": (hidden, dout), "b3": (dout,)}
 
@@ -30,6 +31,7 @@ def flatten(P):
 
 
 def unflatten(flat, din=8, hidden=64, dout=7):
+    """Inverse of `flatten`: a flat parameter vector to the named arrays."""
     out, o = {}, 0
     for k in NAMES:
         shp = shapes(din, hidden, dout)[k]
@@ -40,6 +42,8 @@ def unflatten(flat, din=8, hidden=64, dout=7):
 
 
 def forward(X, P):
+    """Decoder forward pass H1 = relu(X W1 + b1), H2 = relu(H1 W2 + b2),
+    Y = H2 W3 + b3; returns (Y, cache of the activations for `backward`)."""
     X = np.asarray(X, dtype=np.float64)
     A1 = X @ P["W1"] + P["b1"]
     H1 = np.maximum(A1, 0.0)
@@ -50,6 +54,7 @@ def forward(X, P):
 
 
 def loss(Y, T):
+    """Mean squared error over every output value."""
     d = np.asarray(Y) - np.asarray(T, dtype=np.float64)
     return float(np.sum(d * d) / Y.shape[0])
 

@@ -12,6 +12,9 @@ from . import mlp
 
 
 class NeuralTexture2D:
+    """Neural texture: latent levels decoded by the MLP, then stored fallback levels.
+    `fetch` returns decoded texels for latent levels and stored texels above them."""
+
     def __init__(self, latents, params, fallback=()):
         self.latents = [np.asarray(l, dtype=np.float64) for l in latents]
         self.fallback = [np.asarray(f, dtype=np.float64) for f in fallback]
@@ -20,13 +23,16 @@ class NeuralTexture2D:
         self.channels = self.P["W3"].shape[1]
 
     def size(self, level):
+        """(width, height) of a level."""
         h, w = self.levels[level].shape[:2]
         return w, h
 
     def decode(self, Z):
+        """Decoder output for latent rows Z."""
         return mlp.forward(Z, self.P)[0]
 
     def fetch(self, level, ix, iy):
+        """Texels (N, 7) at clamped (ix, iy) of level(s)."""
         level = np.asarray(level, dtype=np.int64)
         ix = np.asarray(ix, dtype=np.int64)
         iy = np.asarray(iy, dtype=np.int64)

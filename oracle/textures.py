@@ -39,6 +39,7 @@ class Texture2D:
         return Texture2D(levels)
 
     def size(self, level):
+        """(width, height) of a level."""
         h, w, _ = self.levels[level].shape
         return w, h
 
@@ -64,6 +65,7 @@ class Dense3D:
         self.channels = 1
 
     def fetch(self, ix, iy, iz):
+        """Values (N, 1) at integer voxel positions; the background outside."""
         Z, Y, X = self.values.shape
         ix, iy, iz = (np.asarray(a, dtype=np.int64) for a in (ix, iy, iz))
         inside = (ix >= 0) & (ix < X) & (iy >= 0) & (iy < Y) & (iz >= 0) & (iz < Z)
@@ -99,6 +101,7 @@ class Sparse3D:
         return ((kx + o) << 42) | ((ky + o) << 21) | (kz + o)
 
     def fetch(self, ix, iy, iz):
+        """Values (N, 1) at integer voxel positions; the background outside."""
         ix, iy, iz = (np.asarray(a, dtype=np.int64) for a in (ix, iy, iz))
         lim = self.OFF - 1
         ok = (np.abs(ix >> 3) < lim) & (np.abs(iy >> 3) < lim) & (np.abs(iz >> 3) < lim)
