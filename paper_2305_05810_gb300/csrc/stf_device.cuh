@@ -562,13 +562,15 @@ __device__ __forceinline__ void dct_texel(const Tex2DView& t, int L, int x, int 
   float x0, x1, x2, y0, y1, y2;
   dct_basis(t, x & 7, x0, x1, x2);
   dct_basis(t, y & 7, y0, y1, y2);
-  const float b[6] = {x0 * y0, x1 * y0, x0 * y1, x2 * y0, x1 * y1, x0 * y2};
+  // DC code step folded into its basis product; each channel's AC step multiplies the
+  // sum of its five integer codes times their basis products
+  const float b[6] = {x0 * y0 * (8.0f / 127.0f), x1 * y0, x0 * y1, x2 * y0, x1 * y1, x0 * y2};
 #pragma unroll
   for (int c = 0; c < C; ++c) {
-    float f = (float)(w[c] & 127u) * (8.0f / 127.0f) * b[0];
+    float ac = dct_ac(w[c], 0) * b[1];
 #pragma unroll
-    for (int j = 0; j < 5; ++j) f = fmaf(dct_ac(w[c], j) * t.ac_step[c], b[j + 1], f);
-    v[c] = f;
+    for (int j = 1; j < 5; ++j) ac = fmaf(dct_ac(w[c], j), b[j + 1], ac);
+    v[c] = fmaf(t.ac_step[c], ac, (float)(w[c] & 127u) * b[0]);
   }
 }
 
