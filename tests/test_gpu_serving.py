@@ -101,3 +101,39 @@ def test_host_pipeline_equals_one_device_call():
     pipe.lookup(stf.make_params("linear"), h_q, h_out, stochastic=False)
     torch.cuda.synchronize()
     assert torch.equal(det.cpu(), h_out)
+
+
+@pytest.mark.parametrize("kind", ["tex2d", "sparse", "neural"])
+def test_chunked_calls_equal_one_call(kind):
+    """Splitting a batch into calls with advancing query_offset gives the results of one
+    call (variates keyed by the global query index), for 2D textures with a level of
+    detail, sparse grids and neural textures."""
+    if kind == "tex2d":
+        T = stf.Texture(stf.KIND_TEX2D, synth.texture2d(64, 64, 4, seed=3), dims=(64, 64, 1), channels=4,
+                        mip_levels=7, generate_mips=True)
+        q = synth.uv_queries(50000, seed=4)
+        lod = torch.from_numpy(synth.lods(50000, seed=5, lo=0, hi=6)).cuda()
+        filt = "catmull_rom"
+    elif kind == "sparse":
+        origins, values = synth.sparse_cloud(domain=256, seed=4)
+        T = stf.Texture(stf.KIND_SPARSE3D, values, leaf_origins=origins)
+        q = (origins[np.arange(50000) % len(origins)] + synth.uniform(150000, 6).reshape(-1, 3) * 8).astype(np.float32)
+        lod, filt = None, "bspline3"
+    else:
+        lat, par = synth.neural_init(64, 3, seed=5)
+        pyr = synth.box_levels(synth.material(64, seed=5), 6)
+        fb = np.concatenate([p.reshape(-1, 7) for p in pyr[3:]])
+        T = stf.NeuralTexture(64, 64, 3, 6, lat, par, fb)
+        q = synth.uv_queries(50000, seed=7)
+        lod = torch.from_numpy(synth.lods(50000, seed=8, lo=0, hi=5)).cuda()
+        filt = "linear"
+    d = torch.from_numpy(np.ascontiguousarray(q)).cuda()
+    n = d.shape[0]
+    whole = T.lookup(d, lod, filter=filt, seed=12, query_offset=1000)
+    parts = torch.empty_like(whole)
+    cuts = [0, 1, 129, 4097, 33333, n]
+    for a, b in zip(cuts[:-1], cuts[1:]):
+        p = stf.make_params(filt, seed=12, query_offset=1000 + a)
+        stf.stf_lookup_batch(T.handle, p, d[a:b], None if lod is None else lod[a:b], b - a, parts[a:b])
+    torch.cuda.synchronize()
+    assert torch.equal(whole, parts)
