@@ -145,9 +145,11 @@ def texels_and_weights(st_s, st_t, A, B, C, hs, ht):
     out_s, out_t, out_w = [], [], []
     for it in range(t0, t1 + 1):
         tt = _f(F32(it) - st_t)
-        r2 = _f(_f(_f(A * _f(ss * ss)) + _f(_f(B * ss) * tt)) + _f(C * _f(tt * tt)))
+        # Q = (A ss + B tt) ss + C tt^2, each product and sum rounded to float32 in
+        # this order; Q < 1 bounds the table index by LUT_SIZE - 1
+        r2 = _f(_f(_f(_f(A * ss) + _f(B * tt)) * ss) + _f(C * _f(tt * tt)))
         inside = r2 < F32(1)
-        idx = np.minimum(_f(r2 * F32(LUT_SIZE)).astype(np.int64), LUT_SIZE - 1)
+        idx = _f(r2 * F32(LUT_SIZE)).astype(np.int64)
         w = lut[np.clip(idx, 0, LUT_SIZE - 1)]
         keep = inside & (w > 0)
         out_s.append(np.arange(s0, s1 + 1)[keep])

@@ -128,13 +128,27 @@ __device__ __forceinline__ bool ewa_span_ok(const Ellipse& e) {
   return e.s1 - e.s0 < kEwaMaxSpan && e.t1 - e.t0 < kEwaMaxSpan;
 }
 
-// Weight of texel (is, it); 0 outside the ellipse.
-__device__ __forceinline__ float ewa_weight(const Ellipse& e, const float* lut, int is, float tt) {
+// Terms of Q that are constant along row it: tt = it - st_t, B tt and C tt^2.
+struct EwaRow {
+  float tt, Btt, Ctt2;
+};
+
+__device__ __forceinline__ EwaRow ewa_row(const Ellipse& e, int it) {
+  EwaRow r;
+  r.tt = __fsub_rn((float)it, e.st_t);
+  r.Btt = __fmul_rn(e.B, r.tt);
+  r.Ctt2 = __fmul_rn(e.C, __fmul_rn(r.tt, r.tt));
+  return r;
+}
+
+// Weight of texel (is, it); 0 outside the ellipse.  Q = (A ss + B tt) ss + C tt^2 in
+// that order.  Q < 1 keeps the table index at most kEwaLut - 1; the lower clamp only
+// guards a rounding-negative Q near the centre (index 0 either way).
+__device__ __forceinline__ float ewa_weight(const Ellipse& e, const float* lut, int is, const EwaRow& row) {
   const float ss = __fsub_rn((float)is, e.st_s);
-  const float r2 = __fadd_rn(__fadd_rn(__fmul_rn(e.A, __fmul_rn(ss, ss)), __fmul_rn(__fmul_rn(e.B, ss), tt)),
-                             __fmul_rn(e.C, __fmul_rn(tt, tt)));
+  const float r2 = __fadd_rn(__fmul_rn(__fadd_rn(__fmul_rn(e.A, ss), row.Btt), ss), row.Ctt2);
   if (!(r2 < 1.0f)) return 0.0f;
-  return lut[min((int)__fmul_rn(r2, (float)kEwaLut), kEwaLut - 1)];
+  return lut[max((int)__fmul_rn(r2, (float)kEwaLut), 0)];
 }
 
 struct EwaArgs {
@@ -191,12 +205,11 @@ __global__ void __launch_bounds__(256) k_ewa(Tex2DView t, EwaArgs a, EwaTable ta
           // rescans one row in the common case and repeats exactly the same additions.
           float S = 0.0f;
           float row_end[kEwaRows];
+          // (adding a zero weight leaves a float32 sum unchanged, so texels outside
+          // the ellipse are summed without a test)
           for (int it = e.t0; it <= e.t1; ++it) {
-            const float tt = __fsub_rn((float)it, e.st_t);
-            for (int is = e.s0; is <= e.s1; ++is) {
-              const float w = ewa_weight(e, lut, is, tt);
-              if (w > 0.0f) S = __fadd_rn(S, w);
-            }
+            const EwaRow row = ewa_row(e, it);
+            for (int is = e.s0; is <= e.s1; ++is) S = __fadd_rn(S, ewa_weight(e, lut, is, row));
             if (it - e.t0 < kEwaRows) row_end[it - e.t0] = S;
           }
           const float us = __fmul_rn(unit24(r.x), S);
@@ -209,16 +222,13 @@ __global__ void __launch_bounds__(256) k_ewa(Tex2DView t, EwaArgs a, EwaTable ta
           }
           int cs = INT_MIN, ct = 0;
           for (int it = start; it <= e.t1 && cs == INT_MIN; ++it) {
-            const float tt = __fsub_rn((float)it, e.st_t);
+            const EwaRow row = ewa_row(e, it);
             for (int is = e.s0; is <= e.s1; ++is) {
-              const float w = ewa_weight(e, lut, is, tt);
-              if (w > 0.0f) {
-                Cs = __fadd_rn(Cs, w);
-                if (us < Cs) {
-                  cs = is;
-                  ct = it;
-                  break;
-                }
+              Cs = __fadd_rn(Cs, ewa_weight(e, lut, is, row));
+              if (us < Cs) {   // never true right after a zero weight
+                cs = is;
+                ct = it;
+                break;
               }
             }
           }
@@ -252,10 +262,10 @@ __global__ void __launch_bounds__(256) k_ewa(Tex2DView t, EwaArgs a, EwaTable ta
 #pragma unroll
           for (int c = 0; c < C; ++c) acc[c] = 0.0f;
           for (int it = e.t0; it <= e.t1; ++it) {
-            const float tt = __fsub_rn((float)it, e.st_t);
+            const EwaRow row = ewa_row(e, it);
             const int cy = min(max(it, 0), HL - 1);
             for (int is = e.s0; is <= e.s1; ++is) {
-              const float w = ewa_weight(e, lut, is, tt);
+              const float w = ewa_weight(e, lut, is, row);
               if (w > 0.0f) {
                 float tv[C];
                 fetch2d<FMT, C>(t, L, min(max(is, 0), WL - 1), cy, tv);
