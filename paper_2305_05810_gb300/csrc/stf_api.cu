@@ -49,7 +49,7 @@ cudaError_t dev_alloc(void** p, size_t bytes) {
   return cudaMalloc(p, bytes);
 }
 
-int grid_blocks(int64_t n, int threads) {
+int grid_blocks(int64_t n, int threads, int waves) {
   static int sm_count[64] = {0};
   int dev = 0;
   cudaGetDevice(&dev);
@@ -59,7 +59,7 @@ int grid_blocks(int64_t n, int threads) {
       sms = 1;
   }
   const int64_t need = (n + threads - 1) / threads;
-  const int64_t cap = (int64_t)sms * (2048 / threads) * 4;   // a few waves, then grid-stride
+  const int64_t cap = (int64_t)sms * (2048 / threads) * waves;   // some waves, then grid-stride
   const int64_t b = need < cap ? need : cap;
   return (int)(b < 1 ? 1 : b);
 }

@@ -105,6 +105,24 @@ template <> struct Filter<STF_FILTER_CATMULL_ROM_POSITIVIZED> : Filter<STF_FILTE
 // and S >= 1, the float32 product u*S is always below S, so that k equals the
 // number of interior boundaries C_0 .. C_{T-2} that are <= u*S; zero-weight taps
 // (C_k == C_{k-1}) are skipped by construction.
+// Number of the boundaries c[0] <= c[1] <= ... <= c[T-2] that are <= v.  Every caller's
+// boundaries are non-decreasing (running sums of |w|, or the closed forms, whose
+// neighbours differ by a weight of at least 1/6), so for four taps the comparison with
+// the middle boundary picks the half and one more comparison the tap: the same count
+// with two comparisons instead of three.
+template <int T>
+__device__ __forceinline__ int boundaries_below(float v, const float* c) {
+  if constexpr (T == 4) {
+    const bool upper = v >= c[1];
+    return (upper ? 2 : 0) + ((v >= (upper ? c[2] : c[0])) ? 1 : 0);
+  } else {
+    int k = 0;
+#pragma unroll
+    for (int j = 0; j < T - 1; ++j) k += (v >= c[j]) ? 1 : 0;
+    return k;
+  }
+}
+
 template <int T>
 struct TapPick {
   int k;
@@ -121,10 +139,7 @@ __device__ __forceinline__ TapPick<T> choose_tap(float u, const float* w) {
   for (int k = 1; k < T; ++k) p.c[k] = __fadd_rn(p.c[k - 1], fabsf(w[k]));
   p.S = p.c[T - 1];
   p.us = __fmul_rn(u, p.S);
-  int k = 0;
-#pragma unroll
-  for (int j = 0; j < T - 1; ++j) k += (p.us >= p.c[j]) ? 1 : 0;
-  p.k = k;
+  p.k = boundaries_below<T>(p.us, p.c);
   return p;
 }
 
@@ -188,10 +203,7 @@ __device__ __forceinline__ float pick_taps(const float* x, const float* u, int* 
       const int b = axis_base(x[a], f);
       float c[Fl::T - 1];
       Fl::cdf(f, c);
-      int k = 0;
-#pragma unroll
-      for (int j = 0; j < Fl::T - 1; ++j) k += (u[a] >= c[j]) ? 1 : 0;
-      idx[a] = b + Fl::OFF0 + k;
+      idx[a] = b + Fl::OFF0 + boundaries_below<Fl::T>(u[a], c);
     }
     return 1.0f;
   }
@@ -225,11 +237,7 @@ __device__ __forceinline__ float pick_taps_r(const float* x, const uint4& r, int
       const int b = axis_base(x[a], f);
       float c[Fl::T - 1];
       Fl::cdf24(f, c);
-      const float R = (float)(w[a] >> 8);
-      int k = 0;
-#pragma unroll
-      for (int j = 0; j < Fl::T - 1; ++j) k += (R >= c[j]) ? 1 : 0;
-      idx[a] = b + Fl::OFF0 + k;
+      idx[a] = b + Fl::OFF0 + boundaries_below<Fl::T>((float)(w[a] >> 8), c);
     }
     return 1.0f;
   } else {
@@ -282,6 +290,15 @@ struct LookupArgs {
   const float* normals;
   float tri_scale;
 };
+
+// Calls without a binning permutation or tap output and with at most 2^30 queries
+// run the stochastic kernels' loops on 32-bit indices, without the per-query pointer
+// tests (3 i + 2 then stays below 2^32); other calls take the general 64-bit loop.
+constexpr int64_t kFastLoopMaxQueries = int64_t(1) << 30;
+
+__device__ __forceinline__ bool fast_loop(const LookupArgs& a) {
+  return a.perm == nullptr && a.taps == nullptr && a.n <= kFastLoopMaxQueries;
+}
 
 __device__ __forceinline__ int64_t query_slot(const LookupArgs& a, int64_t i) {
   return a.perm ? (int64_t)__ldg(a.perm + i) : i;

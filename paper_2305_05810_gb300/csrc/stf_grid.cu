@@ -13,22 +13,29 @@ namespace stf {
 
 // ---------------------------------------------------------------- dense 3D
 
-template <int FMT>
+// Voxel (ix, iy, iz), or the background outside the grid.  OFF32: the grid has at
+// most 2^32 voxels, so the element offset is computed in 32 bits.
+template <int FMT, bool OFF32 = false>
 __device__ __forceinline__ float dense_fetch(const Dense3DView& g, int ix, int iy, int iz) {
   if ((unsigned)ix >= (unsigned)g.nx || (unsigned)iy >= (unsigned)g.ny ||
       (unsigned)iz >= (unsigned)g.nz)
     return g.background;
-  const int64_t e = ((int64_t)iz * g.ny + iy) * g.nx + ix;
+  int64_t e;
+  if constexpr (OFF32)
+    e = (uint32_t)(((uint32_t)iz * (uint32_t)g.ny + (uint32_t)iy) * (uint32_t)g.nx + (uint32_t)ix);
+  else
+    e = ((int64_t)iz * g.ny + iy) * g.nx + ix;
   if constexpr (FMT == STF_FMT_F16)
     return __half2float(__ldg(reinterpret_cast<const __half*>(g.texels) + e));
   else
     return __ldg(reinterpret_cast<const float*>(g.texels) + e);
 }
 
-template <int F, int FMT, bool REUSE>
+// One stochastic lookup of query i (caller's index j).  I is int64_t, or uint32_t in
+// the fast loop (3 i + 2 < 2^32 there).
+template <int F, int FMT, bool REUSE, bool OFF32 = false, typename I>
 __device__ __forceinline__ float dense_stochastic_one(const Dense3DView& g, const LookupArgs& a,
-                                                      int64_t i, int64_t j, uint32_t sample,
-                                                      int4& tap) {
+                                                      I i, I j, uint32_t sample, int4& tap) {
   float x[3] = {__ldg(a.coords + 3 * i), __ldg(a.coords + 3 * i + 1), __ldg(a.coords + 3 * i + 2)};
   if (!prepare_coords<3>(x)) {
     tap = make_int4(0, 0, 0, -1);
@@ -39,7 +46,7 @@ __device__ __forceinline__ float dense_stochastic_one(const Dense3DView& g, cons
     int idx[3];
     pick_fis<F, 3>(x, a, j, sample, r, idx);
     tap = make_int4(idx[0], idx[1], idx[2], 0);
-    return dense_fetch<FMT>(g, idx[0], idx[1], idx[2]);
+    return dense_fetch<FMT, OFF32>(g, idx[0], idx[1], idx[2]);
   } else if constexpr (F == STF_FILTER_CATMULL_ROM_POSITIVIZED) {
     const uint4 r1 = query_variates(a, j, sample, 1u);
     const float up[4] = {unit24(r.x), unit24(r.y), unit24(r.z), unit24(r.w)};
@@ -48,14 +55,14 @@ __device__ __forceinline__ float dense_stochastic_one(const Dense3DView& g, cons
     float Wp, Wn;
     pick_positivized<3>(x, up, un, ip, in, Wp, Wn);
     tap = make_int4(ip[0], ip[1], ip[2], 0);
-    float t = Wp * dense_fetch<FMT>(g, ip[0], ip[1], ip[2]);
-    if (Wn > 0.0f) t = fmaf(-Wn, dense_fetch<FMT>(g, in[0], in[1], in[2]), t);
+    float t = Wp * dense_fetch<FMT, OFF32>(g, ip[0], ip[1], ip[2]);
+    if (Wn > 0.0f) t = fmaf(-Wn, dense_fetch<FMT, OFF32>(g, in[0], in[1], in[2]), t);
     return t;
   } else {
     int idx[3];
     const float sigma = pick_taps_r<F, 3, REUSE>(x, r, idx);
     tap = make_int4(idx[0], idx[1], idx[2], 0);
-    float t = dense_fetch<FMT>(g, idx[0], idx[1], idx[2]);
+    float t = dense_fetch<FMT, OFF32>(g, idx[0], idx[1], idx[2]);
     if constexpr (!Filter<F>::NONNEG) t *= sigma;
     return t;
   }
@@ -63,6 +70,14 @@ __device__ __forceinline__ float dense_stochastic_one(const Dense3DView& g, cons
 
 template <int F, int FMT, bool REUSE>
 __global__ void __launch_bounds__(256) k_dense_stochastic(Dense3DView g, LookupArgs a) {
+  if (fast_loop(a) && (uint64_t)g.nx * (uint64_t)g.ny * (uint64_t)g.nz <= (uint64_t(1) << 32)) {
+    const uint32_t n = (uint32_t)a.n, stride = gridDim.x * blockDim.x;
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+      int4 tap;
+      a.out[i] = dense_stochastic_one<F, FMT, REUSE, true>(g, a, i, i, a.sample_index, tap);
+    }
+    return;
+  }
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += stride) {
     int4 tap;
@@ -138,7 +153,7 @@ cudaError_t launch_tex2d(Op op, int filter, int fmt, int channels, const Tex2DVi
 template <int F, int FMT>
 static cudaError_t run_dense(Op op, const Dense3DView& g, const LookupArgs& a, cudaStream_t s) {
   const int threads = 256;
-  const int blocks = grid_blocks(a.n, threads);
+  const int blocks = grid_blocks(a.n, threads, op == OP_STOCHASTIC ? kStochasticWaves : 4);
   if (op == OP_STOCHASTIC) {
     if constexpr (UsesReuse<F>::value) {
       if (a.reuse) k_dense_stochastic<F, FMT, true><<<blocks, threads, 0, s>>>(g, a);

@@ -296,9 +296,11 @@ __device__ __forceinline__ void stage_upper(const SparseDev& g, UpperSmem& su) {
   __syncthreads();
 }
 
-template <int F, int FMT, bool REUSE>
+// One stochastic lookup of query i (caller's index j).  I is int64_t, or uint32_t in
+// the fast loop (3 i + 2 < 2^32 there).
+template <int F, int FMT, bool REUSE, typename I>
 __device__ __forceinline__ float sparse_stochastic_one(const SparseDev& g, const UpperSmem& su,
-                                                       const LookupArgs& a, int64_t i, int64_t j,
+                                                       const LookupArgs& a, I i, I j,
                                                        uint32_t sample, int4& tap) {
   float x[3] = {__ldg(a.coords + 3 * i), __ldg(a.coords + 3 * i + 1), __ldg(a.coords + 3 * i + 2)};
   if (!prepare_coords<3>(x)) {
@@ -337,6 +339,14 @@ template <int F, int FMT, bool REUSE>
 __global__ void __launch_bounds__(256) k_sparse_stochastic(SparseDev g, LookupArgs a) {
   __shared__ UpperSmem su;
   stage_upper(g, su);
+  if (fast_loop(a)) {
+    const uint32_t n = (uint32_t)a.n, stride = gridDim.x * blockDim.x;
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+      int4 tap;
+      a.out[i] = sparse_stochastic_one<F, FMT, REUSE>(g, su, a, i, i, a.sample_index, tap);
+    }
+    return;
+  }
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += stride) {
     int4 tap;
@@ -424,7 +434,7 @@ __global__ void __launch_bounds__(256) k_sparse_accumulate(SparseDev g, LookupAr
 template <int F, int FMT>
 static cudaError_t run_sparse(Op op, const SparseDev& g, const LookupArgs& a, cudaStream_t s) {
   const int threads = 256;
-  const int blocks = grid_blocks(a.n, threads);
+  const int blocks = grid_blocks(a.n, threads, op == OP_STOCHASTIC ? kStochasticWaves : 4);
   if (op == OP_STOCHASTIC) {
     if constexpr (UsesReuse<F>::value) {
       if (a.reuse) k_sparse_stochastic<F, FMT, true><<<blocks, threads, 0, s>>>(g, a);

@@ -83,9 +83,11 @@ __device__ __forceinline__ void tex2d_stochastic_at(const Tex2DView& t, const Lo
   }
 }
 
-template <int F, int FMT, int C, bool REUSE>
+// One stochastic lookup of query i (caller's index j); I is int64_t, or uint32_t in the
+// fast loop.
+template <int F, int FMT, int C, bool REUSE, typename I>
 __device__ __forceinline__ void tex2d_stochastic_one(const Tex2DView& t, const LookupArgs& a,
-                                                     int64_t i, int64_t j, uint32_t sample,
+                                                     I i, I j, uint32_t sample,
                                                      float* v, int4& tap) {
   const float2 uv = reinterpret_cast<const float2*>(a.coords)[i];
   const float lod = a.lod ? a.lod[i] : 0.0f;
@@ -171,6 +173,16 @@ __device__ __forceinline__ void tex2d_det_at(const Tex2DView& t, const LookupArg
 
 template <int F, int FMT, int C, bool REUSE>
 __global__ void __launch_bounds__(256) k_tex2d_stochastic(Tex2DView t, LookupArgs a) {
+  if (fast_loop(a)) {
+    const uint32_t n = (uint32_t)a.n, stride = gridDim.x * blockDim.x;
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+      float v[C];
+      int4 tap;
+      tex2d_stochastic_one<F, FMT, C, REUSE>(t, a, i, i, a.sample_index, v, tap);
+      store_out<C>(a.out, i, v);
+    }
+    return;
+  }
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += stride) {
     float v[C];

@@ -1,0 +1,85 @@
+"""The stochastic kernels of dense, sparse and 2D textures run calls that ask for no tap
+output and no binning on 32-bit indices (a loop of their own, with 32-bit voxel offsets
+on dense grids).  The parity tests check the general loop against the oracle with tap
+output on; here the same calls without tap output must give bit-identical results, for
+every filter, on inputs that include NaN, huge and out-of-range coordinates."""
+import numpy as np
+import pytest
+import torch
+
+import paper_2305_05810_gb300 as stf
+import synth
+from parity import dev, to_dev
+
+pytestmark = pytest.mark.gpu
+
+FILTERS = ["linear", "bspline3", "catmull_rom", "catmull_rom_positivized", "fis_linear",
+           "fis_bspline3", "fis_gaussian"]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    stf.load()
+
+
+def _edge(d):
+    return np.array([[np.nan] * d, [1e30] * d, [-1e30] * d, [16777216.0] * d, [-16777217.0] * d,
+                     [0.0] * d, [-0.5] * d, [np.inf] + [0.0] * (d - 1)], dtype=np.float32)
+
+
+def _same(T, q, lod=None, **params):
+    """One call with tap output (general loop), one without (fast loop): bit-equal."""
+    n = q.shape[0]
+    taps = torch.empty((n, 4), dtype=torch.int32, device=dev())
+    general = T.lookup(q, lod, taps=taps, **params)
+    fast = T.lookup(q, lod, **params)
+    torch.cuda.synchronize()
+    torch.testing.assert_close(fast, general, rtol=0, atol=0, equal_nan=True)
+
+
+def _params(filt):
+    return {"filter": filt, "seed": 99, "sample_index": 3, "query_offset": 12345,
+            "width": 0.9 if filt == "fis_gaussian" else 0.0}
+
+
+@pytest.mark.parametrize("fmt", [stf.FMT_F32, stf.FMT_F16])
+@pytest.mark.parametrize("filt", FILTERS)
+def test_dense_fast_loop_equals_general_loop(filt, fmt):
+    vals = synth.dense_density(n=40, seed=6, period=9.0)
+    T = stf.Texture(stf.KIND_DENSE3D, vals, dims=(40, 40, 40), fmt=fmt)
+    q = (synth.uniform(3 * 70001, 8).reshape(-1, 3) * np.float32(48) - np.float32(4)).astype(np.float32)
+    _same(T, to_dev(np.concatenate([q, _edge(3)])), **_params(filt))
+
+
+@pytest.mark.parametrize("fmt", [stf.FMT_F32, stf.FMT_E4M3_SCALED])
+@pytest.mark.parametrize("filt", FILTERS)
+def test_sparse_fast_loop_equals_general_loop(filt, fmt):
+    origins, values = synth.sparse_cloud(domain=512, seed=9)
+    T = stf.Texture(stf.KIND_SPARSE3D, values, fmt=fmt, leaf_origins=origins)
+    o = origins[np.arange(60000) % len(origins)].astype(np.float32)
+    q = (o + synth.uniform(3 * 60000, 10).reshape(-1, 3) * np.float32(10) - np.float32(1)).astype(np.float32)
+    _same(T, to_dev(np.concatenate([q, _edge(3)])), **_params(filt))
+
+
+@pytest.mark.parametrize("C", [1, 2, 4])
+@pytest.mark.parametrize("filt", FILTERS)
+def test_tex2d_fast_loop_equals_general_loop(filt, C):
+    T = stf.Texture(stf.KIND_TEX2D, synth.texture2d(128, 64, C, seed=12), dims=(128, 64, 1), channels=C,
+                    mip_levels=7, generate_mips=True)
+    uv = np.concatenate([synth.uv_queries(50000, seed=13) * np.float32(1.4) - np.float32(0.2), _edge(2)])
+    lod = synth.lods(uv.shape[0], seed=14, lo=-1, hi=7).astype(np.float32)
+    lod[-3:] = [np.nan, np.inf, -np.inf]
+    for level_mode in (stf.LEVEL_NEAREST, stf.LEVEL_STOCHASTIC):
+        _same(T, to_dev(uv.astype(np.float32)), to_dev(lod), level_mode=level_mode, **_params(filt))
+
+
+def test_dct_fast_loop_equals_general_loop():
+    base = synth.texture2d(128, 64, 8, seed=15)
+    T = stf.Texture(stf.KIND_TEX2D, base, dims=(128, 64, 1), channels=8, mip_levels=6,
+                    generate_mips=True, fmt=stf.FMT_DCT6)
+    uv = to_dev(np.concatenate([synth.uv_queries(40000, seed=16), _edge(2)]))
+    lod = to_dev(synth.lods(uv.shape[0], seed=17, lo=0, hi=5).astype(np.float32))
+    for filt in ("linear", "bspline3"):
+        _same(T, uv, lod, **_params(filt))
