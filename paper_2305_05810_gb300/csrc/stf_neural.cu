@@ -16,6 +16,7 @@
 // conflicts).  The weight gradients H^T G reduce over the batch, which is the K
 // dimension of that product; their fragments come from row-major activation tiles
 // through ldmatrix.trans.
+#include <cstddef>
 #include <math.h>
 
 #include "stf_internal.h"
@@ -337,6 +338,9 @@ struct Smem {
   Group grp[2];
   uint32_t tmem;
 };
+// A2 doubles as the 16-byte-aligned staging area of the output rows
+static_assert(offsetof(Smem, grp) % 16 == 0 && offsetof(Group, a2) % 16 == 0 && sizeof(Group) % 16 == 0,
+              "A2 tiles are 16-byte aligned");
 
 }  // namespace tc
 
@@ -530,9 +534,16 @@ __global__ void __launch_bounds__(256, 4) k_neural_stochastic_tc(NeuralDev nd, L
 #pragma unroll
       for (int k = 0; k < 7; ++k) stage[row * 7 + k] = v[k];
       group_sync(g);
-      const int64_t nrows = min((int64_t)tc::ROWS, a.n - tile * tc::ROWS);
+      const int nrows = (int)min((int64_t)tc::ROWS, a.n - tile * tc::ROWS);
       float* dst = a.out + tile * tc::ROWS * 7;
-      for (int e = row; e < nrows * 7; e += 128) dst[e] = stage[e];
+      if (nrows == tc::ROWS && (reinterpret_cast<uintptr_t>(dst) & 15) == 0) {
+        // a full tile: 896 floats as 224 16-byte copies
+        const float4* src4 = reinterpret_cast<const float4*>(stage);
+        float4* dst4 = reinterpret_cast<float4*>(dst);
+        for (int e = row; e < tc::ROWS * 7 / 4; e += 128) dst4[e] = src4[e];
+      } else {
+        for (int e = row; e < nrows * 7; e += 128) dst[e] = stage[e];
+      }
     } else if (live) {
 #pragma unroll
       for (int k = 0; k < 7; ++k) a.out[cur.j * 7 + k] = v[k];
