@@ -223,14 +223,19 @@ def test_unbiased_over_4096_samples_c1(filt):
 
 def test_full_size_dense_ray_march_sampled():
     """The benchmark's workload (256^3 FP16, 1920x1080 rays x 16 steps) in the launch
-    configuration the benchmark times; outputs checked on a seeded sample."""
+    configuration the benchmark times (no tap output: the 32-bit-index loop), bit-equal
+    to the same call with tap output; outputs checked on a seeded sample."""
     vals = synth.dense_density(n=256, seed=3)
     q = synth.camera_queries(**synth.C2_RAYS)
     T = stf.Texture(stf.KIND_DENSE3D, vals, dims=(256, 256, 256), fmt=stf.FMT_F16)
     d = to_dev(q)
     N = q.shape[0]
+    fast = T.lookup(d, filter="bspline3", seed=2024)
     taps = torch.empty((N, 4), dtype=torch.int32, device=dev())
     sto = T.lookup(d, taps=taps, filter="bspline3", seed=2024)
+    torch.cuda.synchronize()
+    torch.testing.assert_close(fast, sto, rtol=0, atol=0)
+    del fast
     det = T.lookup_deterministic(d, filter="bspline3")
     idx = np.sort(np.random.default_rng(0).choice(N, 1 << 15, replace=False))
     ref = textures.Dense3D(quantise(vals, stf.FMT_F16))
@@ -239,6 +244,29 @@ def test_full_size_dense_ray_march_sampled():
     check_stochastic(sto.cpu().numpy()[idx], taps.cpu().numpy()[idx], rv, rt, ex)
     dv, _, _ = filters.lookup_3d(ref, q[idx], "bspline3", stochastic_form=False)
     check_deterministic(det.cpu().numpy()[idx], dv, 0.0)
+    stf.stf_synchronize(T.handle)
+
+
+def test_full_size_tex2d_sampled():
+    """The 2D benchmark workload (256^2 RGBA FP32, 16,777,216 uniform uv, B-spline
+    bicubic) in the launch configuration the benchmark times (no tap output), bit-equal
+    to the same call with tap output, and checked on a seeded sample against the
+    oracle."""
+    tex = synth.texture2d(256, 256, 4, seed=1)
+    T = stf.Texture(stf.KIND_TEX2D, tex, dims=(256, 256, 1), channels=4)
+    n = 1 << 24
+    uv = synth.uv_queries(n, seed=2)
+    d = to_dev(uv)
+    fast = T.lookup(d, filter="bspline3", seed=2024)
+    taps = torch.empty((n, 4), dtype=torch.int32, device=dev())
+    sto = T.lookup(d, taps=taps, filter="bspline3", seed=2024)
+    torch.cuda.synchronize()
+    torch.testing.assert_close(fast, sto, rtol=0, atol=0)
+    idx = np.sort(np.random.default_rng(1).choice(n, 1 << 14, replace=False))
+    ref = textures.Texture2D([tex.astype(np.float64)])
+    rv, rt, ex = filters.lookup_2d(ref, uv[idx], None, "bspline3", stochastic_form=True, seed=2024,
+                                   qid=idx.astype(np.uint64))
+    check_stochastic(fast.cpu().numpy()[idx], taps.cpu().numpy()[idx], rv, rt, ex)
     stf.stf_synchronize(T.handle)
 
 

@@ -162,7 +162,8 @@ def _touched_leaves(origins, pts):
 def test_full_size_sparse_ray_march_sampled():
     """2048^3 domain, ~4% active leaves, 2048x2048 rays x 16 steps (67,108,864 queries),
     FP32 and E4M3 leaves, tricubic; checked on a seeded sample of queries against an
-    oracle store holding every leaf those queries can reach."""
+    oracle store holding every leaf those queries can reach, and the benchmark's call
+    without tap output bit-equal to the call with it."""
     origins, values = synth.sparse_cloud(domain=2048, seed=4)
     assert 0.038 < len(origins) / 256 ** 3 < 0.042
     q = synth.camera_queries(**synth.C3_RAYS)
@@ -179,6 +180,11 @@ def test_full_size_sparse_ray_march_sampled():
             ref = textures.Sparse3D(origins[sub], values[sub])
         taps = torch.empty((N, 4), dtype=torch.int32, device=dev())
         sto = T.lookup(d, taps=taps, filter="bspline3", seed=3)
+        # the benchmark's call (no tap output: the 32-bit-index loop) gives the same values
+        fast = T.lookup(d, filter="bspline3", seed=3)
+        torch.cuda.synchronize()
+        torch.testing.assert_close(fast, sto, rtol=0, atol=0)
+        del fast
         rv, rt, ex = filters.lookup_3d(ref, q[idx], "bspline3", stochastic_form=True, seed=3,
                                        qid=idx.astype(np.uint64))
         check_stochastic(sto.cpu().numpy()[idx], taps.cpu().numpy()[idx], rv, rt, ex)
