@@ -240,7 +240,7 @@ def test_full_size_dct_plane_sampled():
     sto = T.lookup(d_uv, lod, taps=taps, filter="linear", seed=2024)
     torch.cuda.synchronize()
     torch.testing.assert_close(fast, sto, rtol=0, atol=0)
-    idx = np.sort(np.random.default_rng(2).choice(n, 1 << 14, replace=False))
+    idx = np.sort(np.random.default_rng(2).choice(n, 1 << 20, replace=False))
     lod_s = lod.cpu().numpy()[idx]
     gv, gt = fast.cpu().numpy()[idx].astype(np.float64), taps.cpu().numpy()[idx].astype(np.int64)
     del fast, sto, taps

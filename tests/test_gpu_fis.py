@@ -249,7 +249,7 @@ def test_full_size_dense_fis_bspline3_sampled():
     N = q.shape[0]
     taps = torch.empty((N, 4), dtype=torch.int32, device=dev())
     out = T.lookup(to_dev(q), taps=taps, filter="fis_bspline3", seed=2024)
-    idx = np.sort(np.random.default_rng(1).choice(N, 1 << 15, replace=False))
+    idx = np.sort(np.random.default_rng(1).choice(N, 1 << 20, replace=False))
     ref = textures.Dense3D(quantise(vals, stf.FMT_F16))
     rv, rt, ex = filters.lookup_3d(ref, q[idx], "fis_bspline3", stochastic_form=True, seed=2024,
                                    qid=idx.astype(np.uint64))

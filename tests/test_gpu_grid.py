@@ -237,7 +237,7 @@ def test_full_size_dense_ray_march_sampled():
     torch.testing.assert_close(fast, sto, rtol=0, atol=0)
     del fast
     det = T.lookup_deterministic(d, filter="bspline3")
-    idx = np.sort(np.random.default_rng(0).choice(N, 1 << 15, replace=False))
+    idx = np.sort(np.random.default_rng(0).choice(N, 1 << 20, replace=False))
     ref = textures.Dense3D(quantise(vals, stf.FMT_F16))
     rv, rt, ex = filters.lookup_3d(ref, q[idx], "bspline3", stochastic_form=True, seed=2024,
                                    qid=idx.astype(np.uint64))
@@ -262,7 +262,7 @@ def test_full_size_tex2d_sampled():
     sto = T.lookup(d, taps=taps, filter="bspline3", seed=2024)
     torch.cuda.synchronize()
     torch.testing.assert_close(fast, sto, rtol=0, atol=0)
-    idx = np.sort(np.random.default_rng(1).choice(n, 1 << 14, replace=False))
+    idx = np.sort(np.random.default_rng(1).choice(n, 1 << 20, replace=False))
     ref = textures.Texture2D([tex.astype(np.float64)])
     rv, rt, ex = filters.lookup_2d(ref, uv[idx], None, "bspline3", stochastic_form=True, seed=2024,
                                    qid=idx.astype(np.uint64))

@@ -171,7 +171,7 @@ def test_full_size_neural_sampled():
     """The benchmark's neural workload (4096^2, four 8-channel FP16 latent levels, FP16
     fallback mips, 16,777,216 uv with lod ~ U[0, 4), nearest level, bilinear tap) in the
     benchmark's launch configuration, with the untrained decoder; outputs checked on a
-    seeded sample of 2^14 queries against the oracle's decode."""
+    seeded sample of 2^20 queries against the oracle's decode."""
     size, nlat, nlev = 4096, 4, 13
     lat, par = synth.neural_init(size, nlat, seed=5)
     pyr = synth.box_levels(synth.material(size, seed=5), nlev)
@@ -184,7 +184,7 @@ def test_full_size_neural_sampled():
     out = T.lookup(to_dev(uv), to_dev(lod), taps=taps, filter="linear", seed=2024,
                    level_mode=stf.LEVEL_NEAREST)
     torch.cuda.synchronize()
-    idx = np.sort(np.random.default_rng(3).choice(n, 1 << 14, replace=False))
+    idx = np.sort(np.random.default_rng(3).choice(n, 1 << 20, replace=False))
     ref = neural.NeuralTexture2D(split_levels(h16(lat), size, 0, nlat, 8), stored_params(par),
                                  [h16(p) for p in pyr[nlat:]])
     rv, rt, ex = filters.lookup_2d(ref, uv[idx], lod[idx], "linear", stochastic_form=True, seed=2024,

@@ -169,7 +169,7 @@ def test_full_size_sparse_ray_march_sampled():
     q = synth.camera_queries(**synth.C3_RAYS)
     d = to_dev(q)
     N = q.shape[0]
-    idx = np.sort(np.random.default_rng(1).choice(N, 1 << 14, replace=False))
+    idx = np.sort(np.random.default_rng(1).choice(N, 1 << 20, replace=False))
     sub = _touched_leaves(origins, q[idx])
     for fmt in (stf.FMT_F32, stf.FMT_E4M3_SCALED):
         T = stf.Texture(stf.KIND_SPARSE3D, values, fmt=fmt, leaf_origins=origins)
