@@ -34,6 +34,12 @@ import sys
 import threading
 import time
 
+# The CPU baseline times the oracle on one core: numpy's BLAS pool (used by the neural
+# oracle's matrix products) is held to one thread before numpy loads.  (The input
+# generators' OpenMP loops are not part of any timed region and keep every core.)
+for _v in ("OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+    os.environ.setdefault(_v, "1")
+
 import numpy as np
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -807,6 +813,17 @@ def run_ours(args):
     if not args.quick:
         ps_, ts_ = time_steps(torch, e2e_serial, max(3, args.steps // 2), 2, stream)
         extras["e2e_serial_one_stream"] = {"lookups_per_s": n * len(ps_) / (ts_ / 1000.0)}
+        # the same pinned host buffers passed to the lookup directly: the kernel reads the
+        # coordinates and writes the results across the host link, no staging copies
+        host_bufs = [h_coords, h_out] + ([] if h_lod is None else [h_lod])
+        if all(stf.stf_device_accessible(b) for b in host_bufs):
+            def e2e_zero_copy():
+                stf.stf_lookup_batch(tex.handle, pe, h_coords, h_lod, n, h_out, None, stream)
+
+            pz, tz = time_steps(torch, e2e_zero_copy, max(3, args.steps // 2), 2, stream)
+            extras["e2e_zero_copy"] = {"lookups_per_s": n * len(pz) / (tz / 1000.0),
+                                       "how": "pinned host coordinates in and results out, read and "
+                                              "written by the lookup kernel over the host link"}
     pe2, te2 = time_steps(torch, e2e_step, max(3, args.steps // 2), 2, stream, dist)
     t_e2e = torch.tensor([te2], dtype=torch.float64, device=dev)
     if dist is not None:

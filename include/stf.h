@@ -23,8 +23,13 @@
  *   - Every call returns an stf_status.  On failure stf_last_error() returns a
  *     message for the calling thread.  Argument errors are reported before any
  *     work is queued.
- *   - Device pointers ("d_" prefix) are CUDA device (or managed) memory owned by
- *     the caller; host pointers ("h_" prefix) are ordinary host memory.
+ *   - Device pointers ("d_" prefix) are memory the device can address, owned by the
+ *     caller: CUDA device or managed memory, or page-locked host memory mapped into
+ *     the device's address space (cudaHostAlloc; cudaHostRegister with
+ *     cudaHostRegisterMapped), whose host address is its device address under
+ *     unified addressing.  The kernels then read coordinates and write results across
+ *     the host link with no staging copy (stf_device_accessible checks a pointer).
+ *     Host pointers ("h_" prefix) are ordinary host memory.
  *   - Work is queued on the given CUDA stream (cudaStream_t passed as void*; NULL
  *     is the legacy default stream) and is asynchronous unless stated otherwise.
  *   - n == 0 is a no-op that returns STF_OK.
@@ -382,6 +387,16 @@ stf_status stf_texture_bytes(stf_texture tex, int64_t* out_bytes);
  * STF_ERR_DEVICE_ASSERT if a kernel flagged an inconsistent structure since the
  * last check, STF_ERR_CUDA if the stream reported an error, else STF_OK. */
 stf_status stf_synchronize(stf_texture tex, void* stream);
+
+/* Whether the current device can address `ptr` at that same address (*out = 1):
+ * device or managed memory, or page-locked host memory mapped at its host address;
+ * *out = 0 for other memory (pageable host memory, another process's memory).  With
+ * host memory this lets a caller pass its host buffers to the lookups directly: the
+ * kernels read the coordinates and write the results over the host link, which on
+ * a Grace host moves them faster than staging copies for one pass (it is no
+ * operation of the paper).  Errors: STF_ERR_INVALID_ARGUMENT for a NULL out,
+ * STF_ERR_CUDA if the runtime cannot be queried (no device). */
+stf_status stf_device_accessible(const void* ptr, int32_t* out);
 
 /* Message of the last failed call on this thread ("" if none). */
 const char* stf_last_error(void);

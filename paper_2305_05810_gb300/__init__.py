@@ -14,7 +14,7 @@ __all__ = [
     "StfError", "TextureDesc", "LookupParams", "stf_create_texture", "stf_destroy",
     "stf_lookup_batch", "stf_lookup_batch_deterministic", "stf_lookup_accumulate",
     "stf_lookup_batch_binned_noalloc",
-    "stf_texture_bytes", "stf_synchronize", "stf_last_error", "stf_version", "Texture",
+    "stf_texture_bytes", "stf_synchronize", "stf_device_accessible", "stf_last_error", "stf_version", "Texture",
     "KIND_TEX2D", "KIND_DENSE3D", "KIND_SPARSE3D", "FMT_F32", "FMT_F16", "FMT_E4M3_SCALED",
     "FILTER_LINEAR", "FILTER_BSPLINE3", "FILTER_CATMULL_ROM", "LEVEL_NEAREST",
     "LEVEL_STOCHASTIC", "library_path", "load", "NeuralDesc", "TrainConfig",
@@ -106,6 +106,7 @@ def load(build_if_missing=True):
     lib.stf_lookup_accumulate.argtypes = [VP, P(LookupParams), VP, VP, I64, I32, VP, VP, VP]
     lib.stf_texture_bytes.argtypes = [VP, P(I64)]
     lib.stf_synchronize.argtypes = [VP, VP]
+    lib.stf_device_accessible.argtypes = [VP, P(I32)]
     lib.stf_last_error.restype = ctypes.c_char_p
     lib.stf_last_error.argtypes = []
     lib.stf_version.restype = I32
@@ -125,7 +126,8 @@ def load(build_if_missing=True):
     lib.stf_debug_fail_allocation.restype = None
     for f in ("stf_create_texture", "stf_destroy", "stf_lookup_batch",
               "stf_lookup_batch_deterministic", "stf_lookup_accumulate", "stf_texture_bytes",
-              "stf_synchronize", "stf_lookup_batch_binned_noalloc", "stf_create_neural_texture",
+              "stf_synchronize", "stf_device_accessible", "stf_lookup_batch_binned_noalloc",
+              "stf_create_neural_texture",
               "stf_neural_gradients", "stf_neural_train", "stf_neural_read", "stf_anisotropic_lod",
               "stf_lookup_batch_ewa", "stf_lookup_batch_ewa_deterministic", "stf_ewa_weight_table",
               "stf_lookup_batch_triplanar", "stf_lookup_batch_triplanar_deterministic"):
@@ -255,6 +257,14 @@ def stf_texture_bytes(tex):
     b = ctypes.c_int64()
     _check(load().stf_texture_bytes(tex, ctypes.byref(b)))
     return b.value
+
+
+def stf_device_accessible(x):
+    """True if the current device can address the tensor (or address) x at that same
+    address: device memory, or pinned host memory mapped into the device's space."""
+    v = ctypes.c_int32()
+    _check(load().stf_device_accessible(_ptr(x), ctypes.byref(v)))
+    return bool(v.value)
 
 
 def stf_synchronize(tex, stream=None):

@@ -312,6 +312,26 @@ stf_status stf_texture_bytes(stf_texture t, int64_t* out_bytes) {
   return STF_OK;
 }
 
+stf_status stf_device_accessible(const void* ptr, int32_t* out) {
+  if (!out) return fail(STF_ERR_INVALID_ARGUMENT, "out is NULL");
+  *out = 0;
+  if (!ptr) return STF_OK;
+  cudaPointerAttributes a;
+  cudaError_t e = cudaPointerGetAttributes(&a, ptr);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail_cuda(e, "pointer attributes");
+  }
+  if (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return fail(STF_ERR_CUDA, "no current device");
+    *out = (a.type == cudaMemoryTypeManaged || a.device == dev) ? 1 : 0;
+  } else if (a.type == cudaMemoryTypeHost) {
+    *out = a.devicePointer == ptr ? 1 : 0;
+  }
+  return STF_OK;
+}
+
 stf_status stf_synchronize(stf_texture t, void* stream) {
   if (!handle_ok(t)) return fail(STF_ERR_INVALID_HANDLE, "unknown texture handle");
   cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);

@@ -69,6 +69,9 @@ def test_argument_errors_without_gpu(lib):
     assert lib.stf_anisotropic_lod(bogus, None, 0, ctypes.c_float(8.0), None, None) == 2
     assert lib.stf_lookup_batch_ewa(bogus, ctypes.byref(p), None, None, 0, ctypes.c_float(8.0),
                                     None, None, None) == 2
+    v = ctypes.c_int32(7)
+    assert lib.stf_device_accessible(None, None) == 1            # NULL out
+    assert lib.stf_device_accessible(None, ctypes.byref(v)) == 0 and v.value == 0   # NULL pointer
 
 
 def test_ewa_weight_table_is_the_oracle_table(lib):

@@ -137,3 +137,45 @@ def test_chunked_calls_equal_one_call(kind):
         stf.stf_lookup_batch(T.handle, p, d[a:b], None if lod is None else lod[a:b], b - a, parts[a:b])
     torch.cuda.synchronize()
     assert torch.equal(whole, parts)
+
+
+@pytest.mark.parametrize("kind", ["tex2d", "dense", "sparse", "neural"])
+def test_zero_copy_host_buffers_equal_device_buffers(kind):
+    """Pinned host buffers passed straight to the lookup (the kernel reads the
+    coordinates and writes the results across the host link) give the results of
+    device buffers, bit for bit; stf_device_accessible tells the buffers apart."""
+    if kind == "tex2d":
+        T = stf.Texture(stf.KIND_TEX2D, synth.texture2d(64, 64, 4, seed=3), dims=(64, 64, 1), channels=4,
+                        mip_levels=7, generate_mips=True)
+        q, lod, filt = synth.uv_queries(70000, seed=4), synth.lods(70000, seed=5, lo=0, hi=6), "bspline3"
+    elif kind == "dense":
+        T = stf.Texture(stf.KIND_DENSE3D, synth.dense_density(n=32, seed=3, period=8.0), dims=(32, 32, 32),
+                        fmt=stf.FMT_F16)
+        q = (synth.uniform(3 * 70000, 6).reshape(-1, 3) * np.float32(36) - np.float32(2)).astype(np.float32)
+        lod, filt = None, "catmull_rom"
+    elif kind == "sparse":
+        origins, values = synth.sparse_cloud(domain=256, seed=4)
+        T = stf.Texture(stf.KIND_SPARSE3D, values, leaf_origins=origins)
+        q = (origins[np.arange(70000) % len(origins)] + synth.uniform(210000, 6).reshape(-1, 3) * 8).astype(np.float32)
+        lod, filt = None, "bspline3"
+    else:
+        lat, par = synth.neural_init(64, 3, seed=5)
+        pyr = synth.box_levels(synth.material(64, seed=5), 6)
+        fb = np.concatenate([p.reshape(-1, 7) for p in pyr[3:]])
+        T = stf.NeuralTexture(64, 64, 3, 6, lat, par, fb)
+        q, lod, filt = synth.uv_queries(70000, seed=7), synth.lods(70000, seed=8, lo=0, hi=5), "linear"
+    n, C = q.shape[0], T.channels
+    h_q = torch.from_numpy(np.ascontiguousarray(q)).pin_memory()
+    h_lod = None if lod is None else torch.from_numpy(lod).pin_memory()
+    h_out = torch.full((n, C), -1.0).pin_memory()
+    pageable = torch.empty(16)
+    d_q = h_q.cuda()
+    d_lod = None if h_lod is None else h_lod.cuda()
+    assert stf.stf_device_accessible(h_q) and stf.stf_device_accessible(h_out) and stf.stf_device_accessible(d_q)
+    assert not stf.stf_device_accessible(pageable)
+    p = stf.make_params(filt, seed=31, query_offset=77)
+    want = torch.empty((n, C), device="cuda")
+    stf.stf_lookup_batch(T.handle, p, d_q, d_lod, n, want)
+    stf.stf_lookup_batch(T.handle, p, h_q, h_lod, n, h_out)
+    torch.cuda.synchronize()
+    assert torch.equal(h_out, want.cpu())
