@@ -83,3 +83,32 @@ def test_dct_fast_loop_equals_general_loop():
     lod = to_dev(synth.lods(uv.shape[0], seed=17, lo=0, hi=5).astype(np.float32))
     for filt in ("linear", "bspline3"):
         _same(T, uv, lod, **_params(filt))
+
+
+@pytest.mark.parametrize("kind", ["dense", "tex2d"])
+def test_calls_around_2_30_queries(kind):
+    """The loop switch at 2^30 queries: a call of 2^30 queries (fast loop, 3 i + 2 just
+    below 2^32) and one of 2^30 + 4097 (general 64-bit loop) end with the same values as
+    a small call over their last queries with the matching query offset."""
+    n_big = (1 << 30) + 4097
+    d = 3 if kind == "dense" else 2
+    g = torch.Generator(device=dev()).manual_seed(5)
+    coords = torch.rand((n_big, d), generator=g, device=dev())
+    if kind == "dense":
+        T = stf.Texture(stf.KIND_DENSE3D, synth.dense_density(n=32, seed=3, period=8.0), dims=(32, 32, 32),
+                        fmt=stf.FMT_F16)
+        coords.mul_(36.0).sub_(2.0)
+    else:
+        T = stf.Texture(stf.KIND_TEX2D, synth.texture2d(64, 64, 1, seed=3), dims=(64, 64, 1), channels=1)
+    out = torch.empty((n_big, 1), device=dev())
+    tail = 1 << 16
+    for n in (1 << 30, n_big):
+        stf.stf_lookup_batch(T.handle, stf.make_params("bspline3", seed=8), coords, None, n, out)
+        small = torch.empty((tail, 1), device=dev())
+        stf.stf_lookup_batch(T.handle, stf.make_params("bspline3", seed=8, query_offset=n - tail),
+                             coords[n - tail:n], None, tail, small)
+        torch.cuda.synchronize()
+        assert torch.equal(out[n - tail:n], small)
+        assert torch.equal(out[:tail], T.lookup(coords[:tail], filter="bspline3", seed=8))
+    del coords, out
+    torch.cuda.empty_cache()
