@@ -239,21 +239,28 @@ def test_fis_argument_checks():
     torch.cuda.synchronize()
 
 
-def test_full_size_dense_fis_bspline3_sampled():
-    """The benchmark's dense workload (256^3 FP16, 1920x1080 rays x 16 steps) with the
-    B-spline FIS filter in the benchmark's launch configuration, checked bit for bit
-    on a seeded sample of outputs."""
+@pytest.mark.parametrize("filt,width", [("fis_linear", 0.0), ("fis_bspline3", 0.0), ("fis_gaussian", 1.0)])
+def test_full_size_dense_fis_sampled(filt, width):
+    """The benchmark's dense workload (256^3 FP16, 1920x1080 rays x 16 steps) with each
+    FIS filter as the benchmark times it (Gaussian sigma = 1, no tap output), bit-equal
+    to the call with tap output and checked on a seeded sample of outputs (2^20 for
+    the B-spline, 2^18 for the others)."""
     vals = synth.dense_density(n=256, seed=3)
     q = synth.camera_queries(**synth.C2_RAYS)
     T = stf.Texture(stf.KIND_DENSE3D, vals, dims=(256, 256, 256), fmt=stf.FMT_F16)
     N = q.shape[0]
+    d = to_dev(q)
+    fast = T.lookup(d, filter=filt, seed=2024, width=width)
     taps = torch.empty((N, 4), dtype=torch.int32, device=dev())
-    out = T.lookup(to_dev(q), taps=taps, filter="fis_bspline3", seed=2024)
-    idx = np.sort(np.random.default_rng(1).choice(N, 1 << 20, replace=False))
+    out = T.lookup(d, taps=taps, filter=filt, seed=2024, width=width)
+    torch.cuda.synchronize()
+    torch.testing.assert_close(fast, out, rtol=0, atol=0)
+    m = 1 << (20 if filt == "fis_bspline3" else 18)
+    idx = np.sort(np.random.default_rng(1).choice(N, m, replace=False))
     ref = textures.Dense3D(quantise(vals, stf.FMT_F16))
-    rv, rt, ex = filters.lookup_3d(ref, q[idx], "fis_bspline3", stochastic_form=True, seed=2024,
-                                   qid=idx.astype(np.uint64))
-    _check_fis("fis_bspline3", out.cpu().numpy()[idx], taps.cpu().numpy()[idx], rv, rt, ex)
+    rv, rt, ex = filters.lookup_3d(ref, q[idx], filt, stochastic_form=True, seed=2024,
+                                   qid=idx.astype(np.uint64), width=width or None)
+    _check_fis(filt, out.cpu().numpy()[idx], taps.cpu().numpy()[idx], rv, rt, ex)
 
 
 def test_fis_ignores_reuse_flag():

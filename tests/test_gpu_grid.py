@@ -270,6 +270,36 @@ def test_full_size_tex2d_sampled():
     stf.stf_synchronize(T.handle)
 
 
+@pytest.mark.parametrize("filt", ["linear", "catmull_rom", "catmull_rom_positivized"])
+def test_full_size_dense_other_filters_sampled(filt):
+    """The dense benchmark workload with the other filters the benchmark times
+    (stochastic trilinear, one-tap Catmull-Rom, positivized Catmull-Rom), without tap
+    output as timed, bit-equal to the call with tap output, and checked on a seeded
+    sample of 2^18 queries against the oracle."""
+    vals = synth.dense_density(n=256, seed=3)
+    q = synth.camera_queries(**synth.C2_RAYS)
+    T = stf.Texture(stf.KIND_DENSE3D, vals, dims=(256, 256, 256), fmt=stf.FMT_F16)
+    d = to_dev(q)
+    N = q.shape[0]
+    fast = T.lookup(d, filter=filt, seed=2024)
+    taps = torch.empty((N, 4), dtype=torch.int32, device=dev())
+    sto = T.lookup(d, taps=taps, filter=filt, seed=2024)
+    torch.cuda.synchronize()
+    torch.testing.assert_close(fast, sto, rtol=0, atol=0)
+    idx = np.sort(np.random.default_rng(4).choice(N, 1 << 18, replace=False))
+    ref = textures.Dense3D(quantise(vals, stf.FMT_F16))
+    rv, rt, ex = filters.lookup_3d(ref, q[idx], filt, stochastic_form=True, seed=2024,
+                                   qid=idx.astype(np.uint64))
+    gv, gt = sto.cpu().numpy()[idx], taps.cpu().numpy()[idx]
+    if filt == "catmull_rom_positivized":
+        p = q[idx]
+        _check_positivized(gv, gt, rv, rt, ex, positivized_scale([p[:, 0], p[:, 1], p[:, 2]],
+                                                                 float(np.max(vals))))
+    else:
+        check_stochastic(gv, gt, rv, rt, ex)
+    stf.stf_synchronize(T.handle)
+
+
 def _check_positivized(gpu_val, gpu_taps, rv, rt, ex, scale):
     gpu_val = np.asarray(gpu_val, dtype=np.float64).reshape(rv.shape)
     same = np.all(np.asarray(gpu_taps).reshape(-1, 4) == rt, axis=1)
