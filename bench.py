@@ -243,6 +243,18 @@ KERNEL_SOURCES = {"dense": ("stf_grid.cu",), "tex2d": ("stf_tex2d.cuh", "stf_tex
                   "dct": ("stf_tex2d.cuh", "stf_tex2d_dct.cu")}
 
 
+def stochastic_extra_bytes(workload, name):
+    """Algorithmic bytes per lookup of a stochastic extra: query in, the texel(s) it
+    fetches, result out (the positivized filter fetches up to two texels; binning's own
+    passes are not counted)."""
+    base = ALGO_BYTES.get((workload, "stochastic"))
+    if base is None or not name.startswith("stochastic"):
+        return None
+    if "positivized" in name:
+        return base + {"dense": 2, "sparse": 4, "sparse_e4m3": 5, "tex2d": 16}[workload]
+    return base
+
+
 def kernel_hash(workload):
     """Hash of the sources that build the workload's lookup kernel."""
     h = hashlib.sha256()
@@ -739,12 +751,17 @@ def run_ours(args):
                           tex.handle, pshuf, shuffled, lod_shuf, n, out, None, stream)),
                      ("stochastic_shuffled_binned", lambda: stf.stf_lookup_batch(
                           tex.handle, pshuf_b, shuffled, lod_shuf, n, out, None, stream))]
+        hbm_peak, _ = peaks()
         for name, fn in variants:
             try:
                 p2, t2 = time_steps(torch, fn, max(3, args.steps // 2), 2, stream)
                 nq = min(n, 1 << 20) if name.endswith("first_2^20") else n
                 extras[name] = {"lookups_per_s": nq * len(p2) / (t2 / 1000.0),
                                 "ms_p50": pct(p2, 50), "ms_p99": pct(p2, 99)}
+                b = stochastic_extra_bytes(w["name"], name)
+                if b is not None:
+                    extras[name]["hbm_frac"] = extras[name]["lookups_per_s"] * b / 1e9 / hbm_peak
+                    extras[name]["algorithmic_bytes_per_lookup"] = b
             except stf.StfError as e:
                 extras[name] = {"unavailable": str(e)}
         if w["name"] == "sparse_e4m3":
