@@ -45,6 +45,9 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
+TEXEL_FORMAT = {"dense": "fp16", "sparse": "fp32", "tex2d": "fp32",
+                "sparse_e4m3": "e4m3 + fp32 leaf scale", "neural": "fp16 latents"}
+
 ALGO_BYTES = {  # algorithmic bytes per lookup: query in + texel(s) + result out
     ("dense", "stochastic"): 12 + 2 + 4,
     ("sparse", "stochastic"): 12 + 4 + 4,
@@ -490,9 +493,10 @@ def run_aniso(args):
         "metric": "EWA lookups/s (stochastic, anisotropic minification)", "value": value,
         "unit": "lookups/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": total / args.steps, "ms_best": min(per), "ms_p50": pct(per, 50), "ms_p99": pct(per, 99),
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32 (fp16 texels)",
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
-        "config": {"workload": "aniso: 1024^2 RGBA FP16 + 11 box levels, ground plane at 3840x2160, "
+        "config": {"texel_format": "fp16",
+                   "workload": "aniso: 1024^2 RGBA FP16 + 11 box levels, ground plane at 3840x2160, "
                                "%d queries with uv derivatives, EWA max anisotropy 16" % n,
                    "l2": "inputs and outputs larger than L2"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
@@ -601,8 +605,9 @@ def run_dct(args):
         "metric": "DCT-texture lookups/s (stochastic trilinear)", "value": value, "unit": "lookups/s",
         "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": total / args.steps,
         "ms_best": min(per), "ms_p50": pct(per, 50), "ms_p99": pct(per, 99), "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32 (DCT6 texels)", "data": "synthetic",
-        "config": {"workload": "dct: 4096^2 x 8 channels DCT6 (6 coefficients per 8x8 block, 7/5-bit "
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"texel_format": "dct6",
+                   "workload": "dct: 4096^2 x 8 channels DCT6 (6 coefficients per 8x8 block, 7/5-bit "
                                "codes) + 13 levels, ground plane at 3840x2160, %d queries, anisotropic "
                                "LOD" % n, "l2": "inputs and outputs larger than L2"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
@@ -652,6 +657,7 @@ def run_reference(args):
         "warmup": args.warmup, "ms_per_step": 1000 * total_time / len(rates),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic", "config": {"workload": w["desc"], "filter": args.filter,
+                                         "texel_format": TEXEL_FORMAT.get(w["name"], "fp32"),
                                          "queries_per_step": n_sample},
         "cpu_baseline": {"value": value, "unit": "lookups/s", "cores": 1, "kind": "oracle",
                          "sample": "first %d queries of the workload per step" % n_sample},
@@ -863,9 +869,12 @@ def run_ours(args):
         "value": value, "unit": "lookups/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
-        "dtype": {"dense": "f32 (fp16 texels)", "sparse_e4m3": "f32 (e4m3 texels)"}.get(w["name"], "f32"),
+        # the filter's arithmetic is float32; the neural decode's MMAs take binary16
+        # operands (float32 accumulation)
+        "dtype": "f16" if w["name"] == "neural" else "f32",
         "data": "synthetic",
         "config": {"workload": w["desc"], "filter": filt, "queries_per_step": n,
+                   "texel_format": TEXEL_FORMAT.get(w["name"], "fp32"),
                    "l2": "inputs larger than L2 (query+output arrays %d MB per step)"
                          % ((w["coords"].nbytes + n * C * 4) // 10**6),
                    "parallelism": "replica per GPU" if world > 1 else "single GPU"},
