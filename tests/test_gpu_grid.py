@@ -368,3 +368,38 @@ def test_positivized_unbiased_and_lower_variance_c1():
     v_pos = np.mean(s2 / S - (s / S) ** 2)
     v_cr = np.mean(s2_cr / S - (s_cr / S) ** 2)
     assert v_pos < v_cr
+
+
+@pytest.mark.parametrize("offset,seed", [((1 << 32) - 5000, 7), ((1 << 64) - 5000, 0x123456789ABCDEF0)])
+def test_counter_and_key_words(offset, seed):
+    """q = query_offset + i crosses into the counter's high word (and wraps at 2^64) and
+    the seed fills both key words: taps bit-exact against the oracle for 2D (with
+    mip levels) and dense lookups; the call without tap output gives the same values."""
+    n = 10000
+    tex = synth.texture2d(64, 64, 2, seed=3)
+    T2 = stf.Texture(stf.KIND_TEX2D, tex, dims=(64, 64, 1), channels=2, mip_levels=7, generate_mips=True)
+    uv = synth.uv_queries(n, seed=4)
+    lod = synth.lods(n, seed=5, lo=0, hi=6)
+    vals, pts = _dense(n=32, seed=6)
+    pts = pts[:n]
+    T3 = stf.Texture(stf.KIND_DENSE3D, vals, dims=(32, 32, 32))
+    qid = (np.arange(n, dtype=np.uint64) + np.uint64(offset % (1 << 64)))
+    for T, x, l, ref_fn in (
+            (T2, uv, lod, lambda: filters.lookup_2d(textures.Texture2D.box_pyramid(tex.astype(np.float64), 7),
+                                                    uv, lod, "bspline3", stochastic_form=True, seed=seed,
+                                                    qid=qid)),
+            (T3, pts, None, lambda: filters.lookup_3d(textures.Dense3D(vals.astype(np.float64)), pts, "bspline3",
+                                                      stochastic_form=True, seed=seed, qid=qid))):
+        taps = torch.empty((x.shape[0], 4), dtype=torch.int32, device=dev())
+        dl = None if l is None else to_dev(l)
+        out = T.lookup(to_dev(x), dl, taps=taps, filter="bspline3", seed=seed, query_offset=offset)
+        fast = T.lookup(to_dev(x), dl, filter="bspline3", seed=seed, query_offset=offset)
+        torch.cuda.synchronize()
+        torch.testing.assert_close(fast, out, rtol=0, atol=0, equal_nan=True)
+        rv, rt, ex = ref_fn()
+        gt = taps.cpu().numpy().astype(np.int64)
+        same = np.all(gt == rt, axis=1)
+        assert np.all(same | ex)
+        assert np.mean(same) > 0.99
+        gv = out.cpu().numpy().astype(np.float64)
+        assert np.all(np.abs(gv - rv)[same] <= 2e-6 * np.abs(rv[same]) + 1e-30)
