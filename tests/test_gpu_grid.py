@@ -370,11 +370,14 @@ def test_positivized_unbiased_and_lower_variance_c1():
     assert v_pos < v_cr
 
 
-@pytest.mark.parametrize("offset,seed", [((1 << 32) - 5000, 7), ((1 << 64) - 5000, 0x123456789ABCDEF0)])
-def test_counter_and_key_words(offset, seed):
-    """q = query_offset + i crosses into the counter's high word (and wraps at 2^64) and
-    the seed fills both key words: taps bit-exact against the oracle for 2D (with
-    mip levels) and dense lookups; the call without tap output gives the same values."""
+@pytest.mark.parametrize("offset,seed,sample", [((1 << 32) - 5000, 7, 0),
+                                                ((1 << 64) - 5000, 0x123456789ABCDEF0, 3),
+                                                (11, 2, (1 << 32) - 1)])
+def test_counter_and_key_words(offset, seed, sample):
+    """q = query_offset + i crosses into the counter's high word (and wraps at 2^64),
+    the seed fills both key words and the sample index reaches 2^32 - 1: taps bit-exact
+    against the oracle for 2D (with mip levels) and dense lookups; the call without tap
+    output gives the same values."""
     n = 10000
     tex = synth.texture2d(64, 64, 2, seed=3)
     T2 = stf.Texture(stf.KIND_TEX2D, tex, dims=(64, 64, 1), channels=2, mip_levels=7, generate_mips=True)
@@ -387,13 +390,16 @@ def test_counter_and_key_words(offset, seed):
     for T, x, l, ref_fn in (
             (T2, uv, lod, lambda: filters.lookup_2d(textures.Texture2D.box_pyramid(tex.astype(np.float64), 7),
                                                     uv, lod, "bspline3", stochastic_form=True, seed=seed,
-                                                    qid=qid)),
+                                                    qid=qid, sample_index=sample)),
             (T3, pts, None, lambda: filters.lookup_3d(textures.Dense3D(vals.astype(np.float64)), pts, "bspline3",
-                                                      stochastic_form=True, seed=seed, qid=qid))):
+                                                      stochastic_form=True, seed=seed, qid=qid,
+                                                      sample_index=sample))):
         taps = torch.empty((x.shape[0], 4), dtype=torch.int32, device=dev())
         dl = None if l is None else to_dev(l)
-        out = T.lookup(to_dev(x), dl, taps=taps, filter="bspline3", seed=seed, query_offset=offset)
-        fast = T.lookup(to_dev(x), dl, filter="bspline3", seed=seed, query_offset=offset)
+        out = T.lookup(to_dev(x), dl, taps=taps, filter="bspline3", seed=seed, query_offset=offset,
+                       sample_index=sample)
+        fast = T.lookup(to_dev(x), dl, filter="bspline3", seed=seed, query_offset=offset,
+                        sample_index=sample)
         torch.cuda.synchronize()
         torch.testing.assert_close(fast, out, rtol=0, atol=0, equal_nan=True)
         rv, rt, ex = ref_fn()
