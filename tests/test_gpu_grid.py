@@ -409,3 +409,37 @@ def test_counter_and_key_words(offset, seed, sample):
         assert np.mean(same) > 0.99
         gv = out.cpu().numpy().astype(np.float64)
         assert np.all(np.abs(gv - rv)[same] <= 2e-6 * np.abs(rv[same]) + 1e-30)
+
+
+@pytest.mark.parametrize("filt", ["bspline3", "catmull_rom", "linear"])
+def test_degenerate_sizes(filt):
+    """One-texel and one-texel-wide 2D textures and 1^3 / 2x1x1 dense grids: every tap
+    clamps to the edge (2D) or falls on the background outside the grid (3D); stochastic
+    taps and values and deterministic values match the oracle."""
+    rng = np.random.default_rng(8)
+    uv = rng.uniform(-0.5, 1.5, (3000, 2)).astype(np.float32)
+    for W, H in ((1, 1), (1, 16), (16, 1)):
+        img = rng.uniform(0, 1, (H, W, 4)).astype(np.float32)
+        T = stf.Texture(stf.KIND_TEX2D, img, dims=(W, H, 1), channels=4)
+        ref = textures.Texture2D([img.astype(np.float64)])
+        taps = torch.empty((uv.shape[0], 4), dtype=torch.int32, device=dev())
+        out = T.lookup(to_dev(uv), taps=taps, filter=filt, seed=3)
+        rv, rt, ex = filters.lookup_2d(ref, uv, None, filt, stochastic_form=True, seed=3)
+        torch.cuda.synchronize()
+        check_stochastic(out.cpu().numpy(), taps.cpu().numpy(), rv, rt, ex)
+        det = T.lookup_deterministic(to_dev(uv), filter=filt)
+        dv, _, _ = filters.lookup_2d(ref, uv, None, filt, stochastic_form=False)
+        check_deterministic(det.cpu().numpy(), dv, 4.0)
+    pts = rng.uniform(-2.5, 3.5, (3000, 3)).astype(np.float32)
+    for dims in ((1, 1, 1), (2, 1, 1)):
+        vals = rng.uniform(0.5, 1, dims[::-1]).astype(np.float32)
+        T = stf.Texture(stf.KIND_DENSE3D, vals, dims=dims)
+        ref = textures.Dense3D(vals.astype(np.float64))
+        taps = torch.empty((pts.shape[0], 4), dtype=torch.int32, device=dev())
+        out = T.lookup(to_dev(pts), taps=taps, filter=filt, seed=4)
+        rv, rt, ex = filters.lookup_3d(ref, pts, filt, stochastic_form=True, seed=4)
+        torch.cuda.synchronize()
+        check_stochastic(out.cpu().numpy(), taps.cpu().numpy(), rv, rt, ex)
+        det = T.lookup_deterministic(to_dev(pts), filter=filt)
+        dv, _, _ = filters.lookup_3d(ref, pts, filt, stochastic_form=False)
+        check_deterministic(det.cpu().numpy(), dv, 2.0)
