@@ -898,7 +898,7 @@ def run_ours(args):
         line["config"]["train"] = {"steps": args.train_steps, "batch": 1 << 16,
                                    "loss_first_last": w.get("train_loss")}
         line["config"]["level_mode"] = "nearest (one decode vs four)"
-    if not args.no_cpu_baseline:
+    if not args.no_cpu_baseline and world == 1:     # the CPU baseline is an N = 1 figure
         if w["name"] == "neural":
             p_, z_ = tex.read()
             w["trained_params"], w["trained_latents"] = p_.cpu().numpy(), z_.cpu().numpy()
