@@ -33,7 +33,7 @@ Triplanar mapping (Section 5.2, "Triplanar mapping"; Eq. 3): a query at position
 with unit normal n blends three lookups of one texture at uv = s (p_y, p_z),
 s (p_x, p_z), s (p_x, p_y) (planes YZ, XZ, XY) with weights |n_x|, |n_y|, |n_z| divided
 by their sum.  The stochastic form draws one plane with probability equal to its
-weight (inverse CDF in float32 over the planes in that order, word 2 of the
+weight (inverse CDF in float64 over the planes in that order, word 2 of the
 query's stream 0) and filters that plane's lookup stochastically; the
 deterministic form blends the three deterministic lookups.
 """
@@ -194,17 +194,17 @@ def triplanar_planes(p, n, scale):
 
 
 def choose_plane(a32, u):
-    """Inverse CDF over |n_x|, |n_y|, |n_z| in float32: the number of the first two
-    running sums that are <= u * S.  Returns (plane, exempt within 1e-6)."""
-    c0 = a32[0]
-    c1 = (a32[0] + a32[1]).astype(np.float32)
-    S = (c1 + a32[2]).astype(np.float32)
-    us = (np.asarray(u, dtype=np.float32) * S).astype(np.float32)
+    """Inverse CDF over |n_x|, |n_y|, |n_z| in float64: the number of the first two
+    running sums that are <= u * S.  Returns (plane, exempt: u within 1e-6 of a
+    boundary, where a float32 evaluation may decide otherwise)."""
+    A = np.asarray(a32, dtype=np.float64)
+    c0 = A[0]
+    c1 = A[0] + A[1]
+    S = c1 + A[2]
+    us = np.asarray(u, dtype=np.float64) * S
     k = (us >= c0).astype(np.int64) + (us >= c1).astype(np.int64)
-    A = a32.astype(np.float64)
-    Sx = A.sum(axis=0)
     with np.errstate(divide="ignore", invalid="ignore"):
-        d = np.minimum(np.abs(u - A[0] / Sx), np.abs(u - (A[0] + A[1]) / Sx))
+        d = np.minimum(np.abs(u - c0 / S), np.abs(u - c1 / S))
     return k, d < 1e-6
 
 

@@ -20,10 +20,13 @@ Readings where the paper is silent or inconsistent (all stated in the design not
 * Taps are ordered from low to high coordinate and tap k is the smallest k with
   u * S < C_k, C_k = sum_{j<=k} |w_j|, S = C_last (sampling arrays, Section 2.2).
   If rounding leaves no such k, the last tap with |w| > 0 is taken.
-* The tap decision is taken in float32, the precision of the paper's listings:
-  each weight (evaluated in float64 at the exact fraction x - floor(x)) is rounded
-  to float32, the running sums are float32 and the product u * S is float32.
-  Values, sums and expectations are float64.
+* Every decision is taken in float64 from the definition: the weights are evaluated
+  at the exact fraction x - floor(x), C_k and S are float64 sums of |w|, and the
+  product u * S is float64.  A float32 implementation (the paper's listings are
+  float32) can decide otherwise only where u lies within its rounding error of a
+  boundary C_k / S; `boundary_distance` reports that distance so that callers can
+  exempt queries within 1e-6 of a boundary.  Values, sums and expectations are
+  float64.
 * Variates: independent per axis by default.  With reuse, one variate is carried
   from axis to axis through the remapping of Eq. 4, generalised to several taps:
   u' = (u * S - C_{k-1}) / |w_k|.
@@ -66,21 +69,24 @@ def axis_weights(f, filt):
 
 
 def select_tap(u, w64):
-    """Inverse-CDF tap choice in float32.  Returns (k, remapped variate)."""
-    a32 = np.abs(w64).astype(np.float32)
-    C = np.cumsum(a32, axis=0, dtype=np.float32)
+    """Inverse-CDF tap choice in float64 (sampling arrays, Section 2.2): the smallest
+    k with u * S < C_k, C_k = sum_{j<=k} |w_j|, S = C_last.  Returns (k, the variate
+    remapped into the chosen tap's interval by Eq. 4, u' = (u S - C_{k-1}) / |w_k|)."""
+    a = np.abs(np.asarray(w64, dtype=np.float64))
+    C = np.cumsum(a, axis=0)
     S = C[-1]
-    us = (np.asarray(u, dtype=np.float32) * S).astype(np.float32)
+    us = np.asarray(u, dtype=np.float64) * S
     below = us[None, :] < C
     T = C.shape[0]
     k = np.argmax(below, axis=0)
-    last_pos = T - 1 - np.argmax((a32 > 0)[::-1], axis=0)
-    k = np.where(below.any(axis=0), k, last_pos)
+    last_pos = T - 1 - np.argmax((a > 0)[::-1], axis=0)
+    k = np.where(below.any(axis=0), k, last_pos)      # only if every weight is zero
     cols = np.arange(k.shape[0])
-    c_prev = np.where(k > 0, C[np.maximum(k - 1, 0), cols], np.float32(0))
-    u2 = ((us - c_prev).astype(np.float32) / a32[k, cols]).astype(np.float32)
-    u2 = np.clip(u2, np.float32(0), np.float32(1 - 2.0 ** -24))
-    return k, u2.astype(np.float64)
+    c_prev = np.where(k > 0, C[np.maximum(k - 1, 0), cols], 0.0)
+    with np.errstate(invalid="ignore", divide="ignore"):
+        u2 = (us - c_prev) / a[k, cols]
+    u2 = np.clip(np.nan_to_num(u2), 0.0, np.nextafter(1.0, 0.0))
+    return k, u2
 
 
 def boundary_distance(u, w64):
@@ -199,7 +205,7 @@ def positivized(fetch, xs32, u_pos, u_neg, background=0.0):
     taps by sign (an even number of outer axes is positive).  A set is sampled by
     choosing one of its blocks with probability proportional to its mass (variate
     u[D]), then on each axis a tap of the block's pair with probability proportional
-    to |w| (variate u[a]).  Decisions in float32 as for `stochastic`; the negative
+    to |w| (variate u[a]).  Decisions in float64 as for `stochastic`; the negative
     sample is skipped when W- is zero.  u_pos / u_neg: lists of D + 1 variates.
     Returns (value, positive tap indices, negative tap indices, exempt, finite)."""
     D = len(xs32)
@@ -207,14 +213,12 @@ def positivized(fetch, xs32, u_pos, u_neg, background=0.0):
     frames = [axis_frame(x) for x in xs32]
     finite = np.logical_and.reduce([fin for (_, _, fin) in frames])
     w64 = [axis_weights(f, "catmull_rom") for (_, f, _) in frames]
-    w32 = [np.abs(w).astype(np.float32) for w in w64]
     m64 = _block_masses(w64, D)
-    m32 = _block_masses([w for w in w32], D)     # float32 arithmetic throughout
     exempt = np.zeros(N, dtype=bool)
     out = {}
     with np.errstate(invalid="ignore", divide="ignore"):   # empty sets (W = 0) are unused
         for sign, u in ((1, u_pos), (-1, u_neg)):
-            out[sign] = _sample_set(D, sign, u, w64, m64, m32, frames, exempt)
+            out[sign] = _sample_set(D, sign, u, w64, m64, frames, exempt)
     Wp, ip = out[1]
     Wn, ineg = out[-1]
     val = Wp[:, None] * fetch(*ip)
@@ -226,17 +230,17 @@ def positivized(fetch, xs32, u_pos, u_neg, background=0.0):
     return val, ip, ineg, exempt & finite, finite
 
 
-def _sample_set(D, sign, u, w64, m64, m32, frames, exempt):
+def _sample_set(D, sign, u, w64, m64, frames, exempt):
     """One sign's block and per-axis taps (see `positivized`); updates exempt."""
     blocks = _blocks_of_sign(D, sign)
-    W = np.sum([m64[b] for b in blocks], axis=0)
-    # block choice: inverse CDF over the set's blocks in increasing order
-    C = np.cumsum(np.stack([m32[b] for b in blocks]).astype(np.float32), axis=0, dtype=np.float32)
-    us = (np.asarray(u[D], dtype=np.float32) * C[-1]).astype(np.float32)
+    Wb = np.stack([m64[b] for b in blocks])
+    W = np.sum(Wb, axis=0)
+    # block choice: inverse CDF over the set's blocks in increasing order, float64
+    C = np.cumsum(Wb, axis=0)
+    us = np.asarray(u[D], dtype=np.float64) * C[-1]
     kb = np.sum(us[None, :] >= C[:-1], axis=0)
     chosen = np.asarray(blocks)[kb]
-    Wb = np.stack([m64[b] for b in blocks])
-    interior = np.cumsum(Wb, axis=0)[:-1] / np.where(W > 0, W, 1)
+    interior = C[:-1] / np.where(W > 0, W, 1)
     exempt |= (W > 0) & (np.min(np.abs(np.asarray(u[D])[None, :] - interior), axis=0) < EXEMPT)
     idx = []
     for a in range(D):
@@ -286,14 +290,16 @@ def _level_choice(lod32, nlev, level_mode, u_level, stochastic_form):
         return zero, zero, np.zeros(N), np.zeros(N, dtype=bool)
     lod = np.clip(np.nan_to_num(lod32.astype(np.float32), nan=0.0),
                   np.float32(0), np.float32(nlev - 1)).astype(np.float32)
+    lod = lod.astype(np.float64)
     if level_mode == LEVEL_NEAREST:
-        L = np.floor((lod + np.float32(0.5)).astype(np.float32)).astype(np.int64)
-        L = np.minimum(L, nlev - 1)
-        return L, L, np.zeros(N), np.zeros(N, dtype=bool)
+        h = lod + 0.5                                   # exact in float64
+        L = np.minimum(np.floor(h).astype(np.int64), nlev - 1)
+        exempt = np.abs(h - np.round(h)) < EXEMPT
+        return L, L, np.zeros(N), exempt
     L0 = np.floor(lod).astype(np.int64)
-    a = (lod - np.floor(lod)).astype(np.float64)
+    a = lod - np.floor(lod)
     if stochastic_form:
-        s = (lod + np.asarray(u_level, dtype=np.float32)).astype(np.float32)
+        s = lod + np.asarray(u_level, dtype=np.float64)  # exact: both are short binary fractions
         L = np.minimum(np.floor(s).astype(np.int64), nlev - 1)
         frac_to_boundary = np.abs(a - (1.0 - u_level))
         exempt = (frac_to_boundary < EXEMPT) & (L0 < nlev - 1)

@@ -2,8 +2,9 @@
 library and the oracle, and compare results under the stated tolerances.
 
 Tolerances (from the float32 arithmetic of the kernels):
-* tap indices: bit-exact, except where a variate lies within 1e-6 of a CDF boundary
-  (the oracle reports those as exempt); an exempt tap may differ by one per axis;
+* tap indices: bit-exact against the oracle's float64 decision, except where a
+  variate lies within 1e-6 of a CDF boundary (the oracle reports those as exempt; at
+  most 0.2% of a test's queries); an exempt tap may differ by one per axis;
 * stochastic values: |gpu - ref| <= 2e-6 |ref| (the texel is exact; only the
   float32 scale sign(w) * sum|w| of Catmull-Rom carries rounding);
 * deterministic values: |gpu - ref| <= 2e-6 max(|ref|, sum_i |w_i t_i|), the second
@@ -45,9 +46,14 @@ def abs_weighted_sum(fetch, xs32, filt):
 
 
 def check_stochastic(gpu_val, gpu_taps, ref_val, ref_taps, exempt, dims=3):
-    """Assert tap and value parity; returns the number of exempt queries."""
+    """Assert tap and value parity; returns the number of queries whose taps differ
+    (all of them exempt).  The exempt count is printed and must stay below 0.2% of the
+    queries (a handful for small cases)."""
     gpu_val = np.asarray(gpu_val, dtype=np.float64).reshape(ref_val.shape)
     gpu_taps = np.asarray(gpu_taps, dtype=np.int64).reshape(-1, 4)
+    exempt = np.asarray(exempt, dtype=bool)
+    print("exempt %d of %d queries" % (np.sum(exempt), exempt.size))
+    assert np.sum(exempt) <= max(4, exempt.size // 500), "exempt %d of %d" % (np.sum(exempt), exempt.size)
     same = np.all(gpu_taps == ref_taps, axis=1)
     bad = ~same & ~exempt
     assert not np.any(bad), "tap mismatch at %s: gpu %s ref %s" % (

@@ -1,15 +1,16 @@
 """GPU parity for the anisotropic level of detail and EWA lookups (Sections 4.2, 5.2;
-Appendix B) through the C ABI against the float32-decision / float64-value oracle
-(`oracle/ewa.py`).
+Appendix B) through the C ABI against the float64 oracle (`oracle/ewa.py`).
 
-Bar: every step of the EWA tap decision is an individually rounded float32
-operation in the same order on both sides, so the drawn texel must match bit for
-bit.  The one exception is the level: log2 of the minor axis may differ by an ulp
-between CUDA's log2f and numpy's, so a level choice within 4e-6 of a level boundary
-is exempt (oracle-reported).  Stochastic values are stored texels (exact; levels
-above 0 agree to the float32 rounding of the library's box pyramid, 2e-6 relative).
-Deterministic values: float32 sums of n positive weights and weighted texels, so
-|gpu - ref| <= 2e-6 |ref| + 4 n 2^-24 max|t| per level."""
+Bar: the oracle takes every decision in float64 from the definitions and carries a
+derived bound on any float32 evaluation of the same formulas.  The drawn texel must
+match bit for bit, except for queries the oracle marks exempt: a variate within 1e-6
+of a CDF boundary, a level boundary within the bounded lod's reach, or an inverse-CDF
+choice that weights within their bounds could move.  The exempt count is printed and
+must stay below 0.2% of the queries.  Stochastic values are stored texels (exact;
+levels above 0 agree to the float32 rounding of the library's box pyramid, 2e-6
+relative).  Deterministic values: |gpu - ref| <= 2e-6 |ref| + the oracle's derived
+bound (float32 sums of the weights and weighted texels, and weights whose table entry
+a float32 Q may reach)."""
 import numpy as np
 import pytest
 import torch
@@ -60,12 +61,12 @@ def test_anisotropic_lod_matches_oracle():
     uv, g = _queries(3000, 64, 5)
     for ma in (1.0, 8.0, 64.0):
         lod = T.anisotropic_lod(to_dev(g), ma).cpu().numpy()
-        _, _, r = ewa.footprint(64, 64, g, ma)
-        fin = ewa.footprint_finite(64, 64, g)
-        r = np.clip(r, 0, 6)
-        assert np.all(np.isnan(lod[~fin]))
-        d = np.abs(lod[fin].astype(np.float64) - r[fin])
-        assert np.all(d <= 2.5e-7 * np.maximum(np.abs(r[fin]), 1.0)), np.max(d)
+        fp = ewa.footprint(64, 64, g, ma)
+        fin = fp.finite
+        assert np.all(np.isnan(lod[~fin & ~fp.ambiguous]))
+        lo, hi = np.clip(fp.lod_lo, 0, 6), np.clip(fp.lod_hi, 0, 6)
+        got = lod[fin].astype(np.float64)
+        assert np.all((lo[fin] <= got) & (got <= hi[fin])), np.max(np.abs(got - np.clip(fp.lod[fin], 0, 6)))
 
 
 @pytest.mark.parametrize("level_mode", [stf.LEVEL_NEAREST, stf.LEVEL_STOCHASTIC])
@@ -85,28 +86,11 @@ def test_ewa_stochastic_matches_oracle(level_mode, max_aniso):
     bad = ~same & ~ex
     assert not np.any(bad), "tap mismatch at %s: gpu %s ref %s" % (
         np.nonzero(bad)[0][:5], gt[bad][:5], rt[bad][:5])
-    assert np.sum(ex) <= n // 200
+    print("exempt %d of %d queries, %d of them differ" % (np.sum(ex), n, np.sum(ex & ~same)))
+    assert np.sum(ex) <= n // 500
     gv = out.cpu().numpy().astype(np.float64)
     assert np.all(np.abs(gv - rv)[same] <= 2e-6 * np.abs(rv[same]))
     stf.stf_synchronize(T.handle)
-
-
-def _ntaps(ref, uv, g, ma, level_mode):
-    """Weighted texels per query at each level the deterministic filter visits."""
-    W0, H0 = ref.size(0)
-    major, minor, lod = ewa.footprint(W0, H0, g, ma)
-    out = np.zeros(uv.shape[0])
-    for q in range(uv.shape[0]):
-        if not (np.all(np.isfinite(uv[q])) and ewa.footprint_finite(W0, H0, g[q:q + 1])[0]):
-            continue
-        L0, L1, frac, _ = ewa._levels(lod[q], len(ref.levels), level_mode, 0.0, False)
-        for L in ({L0, L1} if frac > 0 else {L0}):
-            WL, HL = ref.size(L)
-            st = ewa.raster(uv[q], WL, HL)
-            ax = ewa.level_axes(ref, L, (major[0][q:q + 1], major[1][q:q + 1]), (minor[0][q:q + 1], minor[1][q:q + 1]))
-            A, B, C, hs, ht = ewa.ellipse(*[a[0] for a in ax])
-            out[q] = max(out[q], len(ewa.texels_and_weights(st[0], st[1], A, B, C, hs, ht)[2]))
-    return out
 
 
 @pytest.mark.parametrize("level_mode", [stf.LEVEL_NEAREST, stf.LEVEL_STOCHASTIC])
@@ -115,11 +99,13 @@ def test_ewa_deterministic_matches_oracle(level_mode):
     uv, g = _queries(1500, 64, 8)
     ma = 16.0
     out = T.lookup_ewa_deterministic(to_dev(uv), to_dev(g), ma, level_mode=level_mode)
-    rv, _, _ = ewa.lookup(ref, uv, g, ma, stochastic_form=False, level_mode=level_mode)
-    ntap = _ntaps(ref, uv, g, ma, level_mode)
+    rv, _, tol = ewa.lookup(ref, uv, g, ma, stochastic_form=False, level_mode=level_mode)
     err = np.abs(out.cpu().numpy().astype(np.float64) - rv)
-    lim = 2e-6 * np.abs(rv) + (4 * 2 * ntap * 2.0 ** -24)[:, None]
-    assert np.all(err <= lim), np.max(err / lim)
+    ok = np.isfinite(tol)
+    print("level boundary within reach: %d of %d queries" % (np.sum(~ok), len(ok)))
+    assert np.sum(~ok) <= len(ok) // 500
+    lim = 2e-6 * np.abs(rv) + tol[:, None]
+    assert np.all(err[ok] <= lim[ok]), np.max(err[ok] / lim[ok])
 
 
 def test_ewa_unbiased_over_samples():
@@ -188,11 +174,11 @@ def test_ewa_single_level_texture():
     gt = taps.cpu().numpy()
     assert np.all(gt[gt[:, 3] >= 0, 3] == 0)
     same = np.all(gt == rt, axis=1)
-    assert np.all(same | ex) and not np.any(ex)
+    assert np.all(same | ex) and np.sum(ex) <= n // 500
     assert np.array_equal(out.cpu().numpy().astype(np.float64)[same], rv[same])
     det = T.lookup_ewa_deterministic(to_dev(uv), to_dev(g), 8.0)
-    dv, _, _ = ewa.lookup(ref, uv, g, 8.0, stochastic_form=False)
-    assert np.allclose(det.cpu().numpy(), dv, atol=2e-5)
+    dv, _, tol = ewa.lookup(ref, uv, g, 8.0, stochastic_form=False)
+    assert np.all(np.abs(det.cpu().numpy() - dv) <= 2e-6 * np.abs(dv) + tol[:, None])
 
 
 def test_full_size_ewa_plane_sampled():
@@ -221,7 +207,8 @@ def test_full_size_ewa_plane_sampled():
     gt = taps.cpu().numpy()[idx].astype(np.int64)
     same = np.all(gt == rt, axis=1)
     assert not np.any(~same & ~ex)
-    assert np.sum(ex) <= len(idx) // 200
+    print("exempt %d of %d sampled queries" % (np.sum(ex), len(idx)))
+    assert np.sum(ex) <= len(idx) // 500
     gv = out.cpu().numpy()[idx].astype(np.float64)
     assert np.array_equal(gv[same], rv[same])
     stf.stf_synchronize(T.handle)

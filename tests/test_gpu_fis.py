@@ -206,7 +206,7 @@ def test_fis_unbiased_over_4096_samples(filt):
         z = (mean[live, c] - F[live, c]) / np.sqrt(var[live, c] / S)
         assert np.mean(np.abs(z) > 3) <= 0.005, np.mean(np.abs(z) > 3)
         pooled = np.sum(mean[live, c] - F[live, c]) / np.sqrt(np.sum(var[live, c]) / S)
-        assert abs(pooled) <= 4.0, pooled
+        assert abs(pooled) <= 3.0, pooled
 
 
 @pytest.mark.parametrize("filt", FIS)

@@ -198,8 +198,7 @@ def test_unbiased_over_4096_samples_c1(filt):
     """4096 samples per query, float64 accumulators on the GPU; z-scores against the
     oracle's deterministic filter with the estimator's exact variance (enumerated
     second moment).  Per query the |z| > 3 rate must stay <= 0.5% (0.27% expected);
-    the pooled z over all queries must stay within 4 (several channels and filters
-    are tested)."""
+    the pooled z over all queries must stay within +-3."""
     tex, uv = _c1()
     uv = uv[:65536]
     T = stf.Texture(stf.KIND_TEX2D, tex, dims=(256, 256, 1), channels=4)
@@ -218,7 +217,8 @@ def test_unbiased_over_4096_samples_c1(filt):
         z = (mean[live, c] - F[live, c]) / np.sqrt(var[live, c] / S)
         assert np.mean(np.abs(z) > 3) <= 0.005, np.mean(np.abs(z) > 3)
         pooled = np.sum(mean[live, c] - F[live, c]) / np.sqrt(np.sum(var[live, c]) / S)
-        assert abs(pooled) <= 4.0, pooled
+        print("%s channel %d: |z| > 3 rate %.4f, pooled %.3f" % (filt, c, np.mean(np.abs(z) > 3), pooled))
+        assert abs(pooled) <= 3.0, pooled
 
 
 def test_full_size_dense_ray_march_sampled():
@@ -364,7 +364,7 @@ def test_positivized_unbiased_and_lower_variance_c1():
         z = (mean[live, c] - F[live, c]) / np.sqrt(var[live, c] / S)
         assert np.mean(np.abs(z) > 3) <= 0.005
         pooled = np.sum(mean[live, c] - F[live, c]) / np.sqrt(np.sum(var[live, c]) / S)
-        assert abs(pooled) <= 4.0
+        assert abs(pooled) <= 3.0, pooled
     v_pos = np.mean(s2 / S - (s / S) ** 2)
     v_cr = np.mean(s2_cr / S - (s_cr / S) ** 2)
     assert v_pos < v_cr

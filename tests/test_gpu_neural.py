@@ -131,11 +131,12 @@ def test_neural_gradients_match_oracle():
     g = mlp.backward(cache, P, Y, tgt)
     assert abs(loss.item() - mlp.loss(Y, tgt)) <= 2e-3 * mlp.loss(Y, tgt)
     G = mlp.unflatten(pg.cpu().numpy())
+    rels = {}
     for k in mlp.NAMES:
-        rel = np.linalg.norm(G[k] - g[k]) / max(np.linalg.norm(g[k]), 1e-12)
-        assert rel <= 2e-2, (k, rel)
-    rel = np.linalg.norm(lg.cpu().numpy() - g["X"]) / np.linalg.norm(g["X"])
-    assert rel <= 2e-2, rel
+        rels[k] = np.linalg.norm(G[k] - g[k]) / max(np.linalg.norm(g[k]), 1e-12)
+    rels["X"] = np.linalg.norm(lg.cpu().numpy() - g["X"]) / np.linalg.norm(g["X"])
+    print("relative gradient errors (norm):", {k: "%.2e" % v for k, v in rels.items()})
+    assert max(rels.values()) <= 1e-2, rels
 
 
 def test_training_gains_over_untrained_decoder():

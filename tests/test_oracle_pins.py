@@ -31,6 +31,30 @@ def test_philox_round_structure_matches_numpy_philox4x64(ctr, key):
     assert list(philox.philox4x64(c, key)) == ref
 
 
+def test_philox4x32_10_known_answers():
+    """The published known answers of Philox4x32-10 (golden fixture, cited there):
+    they fix the 4x32 multipliers and Weyl constants, which the 4x64 structure pin
+    and the statistical pins cannot."""
+    rows = []
+    with open(os.path.join(GOLDEN, "philox4x32_10_kat.txt")) as fh:
+        for line in fh:
+            if line.strip() and not line.startswith("#"):
+                rows.append([int(w, 16) for w in line.split()])
+    assert len(rows) == 3
+    for r in rows:
+        out = philox.philox4x32(*r[:6])
+        assert [int(x) for x in out] == r[6:]
+
+
+def test_philox_weyl_constants_are_the_published_irrationals():
+    """W0 = floor(2^32 (golden ratio - 1)), W1 = floor(2^32 (sqrt 3 - 1)) (Salmon et al.,
+    Section 4.2), computed here with exact integer square roots."""
+    from math import isqrt
+    w0 = (isqrt(5 << 128) - (1 << 64)) >> 33          # 2^32 (sqrt5 - 1)/2
+    w1 = isqrt(3 << 64) - (1 << 32)                   # 2^32 (sqrt3 - 1)
+    assert philox.PHILOX4X32["W"] == (w0, w1)
+
+
 def test_philox4x32_uniform_chi2_and_exact_variates():
     n = 1 << 20
     u = philox.query_variates(np.arange(n, dtype=np.uint64), 0, 42)
