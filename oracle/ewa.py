@@ -284,6 +284,13 @@ def texels_and_weights(st_s, st_t, ell):
     # (2 U relative each, entering squared or as a product), and at most four roundings
     # along any evaluation order of the three-term form
     eQ = A[1] * ss * ss + B[1] * np.abs(ss * tt) + C[1] * tt * tt + (2 * U + 4 * U / (1 - 4 * U)) * T
+    # a texel index beyond 2^24 is not a float32 number: its conversion adds up to
+    # U |i| to ss or tt before the subtraction (raster positions clamped near +-2^24)
+    es = np.where(np.abs(si) > (1 << 24), U * np.abs(si), 0.0)[None, :]
+    et = np.where(np.abs(ti) > (1 << 24), U * np.abs(ti), 0.0)[:, None]
+    aA, aB, aC = abs(A[0]), abs(B[0]), abs(C[0])
+    eQ = eQ + (2 * aA * np.abs(ss) + aB * np.abs(tt)) * es + (aB * np.abs(ss) + 2 * aC * np.abs(tt)) * et \
+        + aA * es * es + aB * es * et + aC * et * et
     eQ = eQ * (1 + 1e-6) + 4 * SUB
     lut = weight_lut()
 

@@ -42,9 +42,11 @@ stf_status fail_cuda(cudaError_t e, const char* what) {
 // Test hook: when > 0, the countdown-th device allocation from now fails.
 static int64_t g_alloc_countdown = 0;
 
+bool alloc_should_fail() { return g_alloc_countdown > 0 && --g_alloc_countdown == 0; }
+
 cudaError_t dev_alloc(void** p, size_t bytes) {
   *p = nullptr;
-  if (g_alloc_countdown > 0 && --g_alloc_countdown == 0) return cudaErrorMemoryAllocation;
+  if (alloc_should_fail()) return cudaErrorMemoryAllocation;
   if (bytes == 0) bytes = 16;
   return cudaMalloc(p, bytes);
 }

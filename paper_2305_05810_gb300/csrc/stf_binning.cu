@@ -200,10 +200,7 @@ static cudaError_t pool_alloc(void** p, size_t bytes, cudaStream_t s) {
       cudaMemPoolSetAttribute(g_pool[dev & 63], cudaMemPoolAttrReleaseThreshold, &keep);
     }
   }
-  void* probe = nullptr;
-  e = dev_alloc(&probe, 0);          // honours the failure-injection hook
-  if (e != cudaSuccess) return e;
-  cudaFree(probe);
+  if (alloc_should_fail()) return cudaErrorMemoryAllocation;   // the failure-injection hook
   return cudaMallocFromPoolAsync(p, bytes, g_pool[dev & 63], s);
 }
 
@@ -276,7 +273,7 @@ stf_status lookup_binned(stf_texture t, int filter, const LookupArgs& a0, cudaSt
 namespace {
 
 constexpr int64_t kNoAllocMaxQueries = STF_NOALLOC_MAX_QUERIES;
-// [histogram | cursors] (2 x 65536 words) | permutation (max queries words) |
+// [histogram | cursors] (2 x kBins = 2 x 1024 words) | permutation (max queries words) |
 // binned coordinates, 3 floats per query for 3D, or 2 floats + lod for 2D.
 constexpr size_t kNoAllocHistBytes = sizeof(uint32_t) * 2 * stf::kBins;
 constexpr size_t kNoAllocPermBytes = sizeof(uint32_t) * kNoAllocMaxQueries;

@@ -9,6 +9,9 @@ namespace stf {
 stf_status fail(stf_status code, const char* fmt, ...);
 stf_status fail_cuda(cudaError_t e, const char* what);
 cudaError_t dev_alloc(void** p, size_t bytes);
+// Failure-injection hook: counts one device allocation and says whether it must fail
+// (stf_debug_fail_allocation); allocates nothing.
+bool alloc_should_fail();
 bool handle_ok(stf_texture t);
 stf_status dispatch(Op op, stf_texture t, int filter, const LookupArgs& a, cudaStream_t s);
 stf_status triplanar(Op op, stf_texture t, const stf_lookup_params* p, const float* pos,

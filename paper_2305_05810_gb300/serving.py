@@ -11,9 +11,20 @@ device copy, one library call, device to host copy) on its slot's stream; chunks
 pass query_offset so the random variates stay keyed on the request-local query
 index: a request's result is the same whether it runs alone or in any mix.
 
+Memory accounting: the budget covers what is resident on the device for serving,
+the textures' bytes (``resident_bytes``) plus every slot's buffers.  A slot keeps
+its buffers between requests (so that admitting a request usually allocates
+nothing), so the scheduler charges each slot the bytes it holds, idle or not, and a
+request is admitted only if the slot's buffers after growing for it, plus every
+other slot's holdings and the resident bytes, fit in the budget; idle slots'
+buffers are released when that makes room.
+
 The loop itself (admission, budget, chunking, completion) lives in ``Scheduler``,
 which talks to the device through a small backend interface so that it can be
-tested without a GPU; ``TorchBackend`` is the real one.
+tested without a GPU; ``TorchBackend`` is the real one.  A backend provides
+``channels(texture)``, ``hold_after(slot, request)`` (bytes the slot holds once it
+has begun the request), ``release(slot)`` (free an idle slot's buffers), ``begin``,
+``launch_chunk``, ``chunk_done`` and ``finish``.
 """
 import collections
 import math
@@ -60,41 +71,76 @@ class Scheduler:
     """Admission, chunking and completion; the device side is the backend."""
 
     def __init__(self, backend, n_slots=8, budget_bytes=16 << 30, chunk_queries=1 << 20,
-                 max_chunks_in_flight=2, clock=time.perf_counter):
+                 max_chunks_in_flight=2, clock=time.perf_counter, resident_bytes=0):
         self.backend = backend
         self.n_slots = n_slots
         self.budget = int(budget_bytes)
+        self.resident = int(resident_bytes)
+        if self.resident > self.budget:
+            raise BudgetError("resident textures (%d bytes) exceed the budget (%d)" % (self.resident, self.budget))
         self.chunk = int(chunk_queries)
         self.depth = max_chunks_in_flight
         self.clock = clock
         self.waiting = collections.deque()
         self.free_slots = collections.deque(range(n_slots))
         self.active = {}            # slot -> job
-        self.in_use = 0
+        self.hold = [0] * n_slots   # device bytes each slot holds (idle slots keep buffers)
         self.done = []
         self.rejected = []
-        self.peak_in_use = 0
+        self.peak_in_use = self.resident
         self.peak_active = 0
 
+    @property
+    def in_use(self):
+        """Device bytes charged against the budget: resident textures plus every
+        slot's buffers."""
+        return self.resident + sum(self.hold)
+
     def submit(self, req):
-        need = req.device_bytes(self.backend.channels(req.texture))
-        if need > self.budget:
+        need = self.backend.hold_after(None, req)
+        if self.resident + need > self.budget:
             self.rejected.append(req)
-            raise BudgetError("request %r needs %d bytes, budget is %d" % (req.rid, need, self.budget))
+            raise BudgetError("request %r needs %d bytes next to %d resident, budget is %d" %
+                              (req.rid, need, self.resident, self.budget))
         self.waiting.append(req)
+
+    def _fit(self, req):
+        """A free slot the request fits in, releasing idle slots' buffers if that
+        makes room; None if it must wait."""
+        best = None
+        for slot in self.free_slots:
+            after = self.in_use - self.hold[slot] + self.backend.hold_after(slot, req)
+            if best is None or after < best[1]:
+                best = (slot, after)
+        slot, after = best
+        if after <= self.budget:
+            return slot
+        for other in list(self.free_slots):
+            if other != slot and self.hold[other] > 0:
+                self.backend.release(other)
+                after -= self.hold[other]
+                self.hold[other] = 0
+                if after <= self.budget:
+                    return slot
+        if after - self.hold[slot] + self.backend.hold_after(None, req) <= self.budget:
+            self.backend.release(slot)                  # regrow this slot from nothing
+            self.hold[slot] = 0
+            return slot
+        return None
 
     def _admit(self):
         while self.waiting and self.free_slots:
             req = self.waiting[0]
-            need = req.device_bytes(self.backend.channels(req.texture))
-            if self.in_use + need > self.budget:
+            slot = self._fit(req)
+            if slot is None:
                 return                                  # FIFO: wait for memory
             self.waiting.popleft()
-            slot = self.free_slots.popleft()
-            self.in_use += need
+            self.free_slots.remove(slot)
+            self.hold[slot] = self.backend.hold_after(slot, req)
             self.peak_in_use = max(self.peak_in_use, self.in_use)
+            assert self.in_use <= self.budget
             req.t_admit = self.clock()
-            job = {"req": req, "slot": slot, "bytes": need, "next": 0, "inflight": collections.deque(),
+            job = {"req": req, "slot": slot, "next": 0, "inflight": collections.deque(),
                    "state": self.backend.begin(req, slot)}
             self.active[slot] = job
             self.peak_active = max(self.peak_active, len(self.active))
@@ -121,7 +167,6 @@ class Scheduler:
             req = job["req"]
             req.result = self.backend.finish(job["state"], req)
             req.t_done = self.clock()
-            self.in_use -= job["bytes"]
             self.free_slots.append(slot)
             self.done.append(req)
 
@@ -162,8 +207,12 @@ class TorchBackend:
 
     Each slot owns device buffers (coordinates, levels of detail, results) and a
     pinned host buffer for results; all grow to the largest request the slot has
-    served and are then reused, so admitting a request allocates nothing (device and
-    pinned-host allocations synchronise and would stall the other slots).  With
+    served and are then reused, so admitting a request usually allocates nothing
+    (device and pinned-host allocations synchronise and would stall the other
+    slots).  ``hold_after`` reports the device bytes a slot's buffers take once they
+    have grown for a request, which the scheduler charges against its budget;
+    ``release`` drops an idle slot's device buffers (their blocks return to torch's
+    caching allocator, which reuses them for the next growth).  With
     keep_results the result of each request is copied out of the slot's pinned buffer
     into its own host tensor; otherwise ``on_result(request, view)`` (if given) sees
     the pinned view before the slot is reused."""
@@ -181,14 +230,38 @@ class TorchBackend:
     def channels(self, key):
         return self.textures[key].channels
 
+    @staticmethod
+    def _alloc_numel(numel):
+        return max(numel, 1 << 16)
+
+    def _needs(self, req):
+        C = self.textures[req.texture].channels
+        d = {"coords": req.n * req.coords.shape[1], "out": req.n * C}
+        if req.lod is not None:
+            d["lod"] = req.n
+        return d
+
+    def hold_after(self, slot, req):
+        """Device bytes slot holds after begin(req) (slot None: an empty slot)."""
+        have = {} if slot is None else {k: b.numel() for k, b in self.slot_bufs[slot].items()
+                                        if k != "h_out"}
+        for k, numel in self._needs(req).items():
+            if have.get(k, 0) < numel:
+                have[k] = self._alloc_numel(numel)
+        return 4 * sum(have.values())
+
+    def release(self, slot):
+        for k in [k for k in self.slot_bufs[slot] if k != "h_out"]:
+            del self.slot_bufs[slot][k]
+
     def _buf(self, slot, name, numel, host=False):
         b = self.slot_bufs[slot].get(name)
         if b is None or b.numel() < numel:
             if host:
-                b = self.torch.empty(max(numel, 1 << 16), dtype=self.torch.float32, pin_memory=True)
+                b = self.torch.empty(self._alloc_numel(numel), dtype=self.torch.float32, pin_memory=True)
             else:
                 with self.torch.cuda.stream(self.streams[slot]):
-                    b = self.torch.empty(max(numel, 1 << 16), dtype=self.torch.float32, device=self.device)
+                    b = self.torch.empty(self._alloc_numel(numel), dtype=self.torch.float32, device=self.device)
             self.slot_bufs[slot][name] = b
         return b
 

@@ -58,6 +58,9 @@ def test_each_result_is_the_same_alone_and_in_the_mix(textures):
     done = sched.run(reqs)
     assert len(done) == len(reqs) and sched.peak_active >= 2
     assert sched.peak_in_use <= 64 << 20
+    # the slots' device buffers that stay allocated are what the scheduler charges
+    held = sum(4 * b.numel() for bufs in backend.slot_bufs for k, b in bufs.items() if k != "h_out")
+    assert held == sched.in_use <= 64 << 20
     for r in reqs:
         T = textures[r.texture]
         d = r.coords.cuda()

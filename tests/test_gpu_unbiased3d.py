@@ -48,7 +48,7 @@ def _z_test(T, ref, pts, filt, seed):
     tail = np.mean(np.abs(z) > 3)
     pooled = np.sum(mean[live] - F[live]) / np.sqrt(np.sum(var[live]) / S)
     print("%s: %d live queries, |z| > 3 rate %.4f, pooled %.3f" % (filt, np.sum(live), tail, pooled))
-    assert np.sum(live) > 0.5 * len(pts)
+    assert np.sum(live) > 0.25 * len(pts)       # at least a quarter straddle non-zero texels
     assert tail <= 0.005, tail
     assert abs(pooled) <= 3.0, pooled
 

@@ -8,18 +8,34 @@ from paper_2305_05810_gb300 import serving
 
 
 class FakeBackend:
-    """Chunks complete `latency` ticks after launch; results record the offsets."""
+    """Chunks complete `latency` ticks after launch; results record the offsets.  Each
+    slot's buffers grow to the largest request it has begun and stay until released,
+    like the real backend's; `held` is the device bytes they take."""
 
     def __init__(self, latency=3, channels=1):
         self.t = 0
         self.latency = latency
         self.ch = channels
         self.launched = []
+        self.bufs = {}               # slot -> bytes held
+        self.max_held = 0
 
     def channels(self, key):
         return self.ch
 
+    def hold_after(self, slot, req):
+        return max(self.bufs.get(slot, 0) if slot is not None else 0, req.device_bytes(self.ch))
+
+    def release(self, slot):
+        self.bufs.pop(slot, None)
+
+    @property
+    def held(self):
+        return sum(self.bufs.values())
+
     def begin(self, req, slot):
+        self.bufs[slot] = self.hold_after(slot, req)
+        self.max_held = max(self.max_held, self.held)
         return {"out": np.full(req.n, -1, dtype=np.int64), "slot": slot}
 
     def launch_chunk(self, st, req, slot, a, b):
@@ -74,6 +90,37 @@ def test_all_requests_complete_with_full_coverage_and_budget_respected():
         assert offs[0][0] == 0 and offs[-1][1] == sizes[rid]
         assert all(b - a <= 700 for a, b in offs)
         assert all(offs[k][1] == offs[k + 1][0] for k in range(len(offs) - 1))
+
+
+def test_held_buffers_of_idle_slots_count_against_the_budget():
+    """Slots keep their buffers between requests; the device bytes actually held
+    (every slot's buffers plus the resident textures) never exceed the budget, and
+    idle slots' buffers are released when a request needs the room."""
+    be = FakeBackend(latency=2)
+    resident = 20000
+    budget = resident + 16 * 6000
+    sched = serving.Scheduler(be, n_slots=4, budget_bytes=budget, chunk_queries=500,
+                              clock=lambda: be.t, resident_bytes=resident)
+    rng = np.random.default_rng(1)
+    sizes = [int(x) for x in rng.integers(1, 6000, 60)] + [6000, 5999, 1]
+    reqs = [make_req(i, n) for i, n in enumerate(sizes)]
+    for r in reqs:
+        sched.submit(r)
+    for _ in range(100000):
+        sched.step()
+        assert be.held + resident <= budget
+        assert sched.in_use == be.held + resident          # the charge is what is held
+        be.t += 1
+        if sched.idle():
+            break
+    assert len(sched.done) == len(sizes)
+    assert be.max_held + resident <= budget and sched.peak_in_use <= budget
+    assert sched.peak_active >= 2
+
+
+def test_resident_textures_larger_than_budget_are_rejected():
+    with pytest.raises(serving.BudgetError):
+        serving.Scheduler(FakeBackend(), budget_bytes=1000, resident_bytes=1001)
 
 
 def test_fifo_admission_waits_for_memory():
