@@ -411,6 +411,66 @@ def cpu_oracle_rate(w, filt, n_queries):
     return rate, dt, pool.cores
 
 
+def storage_error(stf, torch, w, tex, filt, stream, m=1 << 17, level_mode=None):
+    """Error of the library's stochastic and deterministic lookups on the stored
+    texture (FP16 / E4M3 + leaf scale / FP32; the neural texture's FP16 latents and
+    decoder) against the float64 oracle on the unquantised texels (the float32 values
+    the texture was built from; for the neural texture, the target it was trained on),
+    over m consecutive queries from the middle of the workload.  The stochastic pair
+    draws the same taps (queries whose tap the oracle marks exempt are left out), so
+    its error is the storage error of the fetched texel; the deterministic pair
+    compares the full filters.  Oracle leg only: part of the CPU-baseline run."""
+    from oracle import filters, textures
+    n = w["coords"].shape[0]
+    m = min(m, n)
+    a = (n - m) // 2
+    q = w["coords"][a:a + m]
+    qid = np.arange(a, a + m, dtype=np.uint64)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    d = torch.from_numpy(np.ascontiguousarray(q)).to(dev)
+    lod = w["lod"][a:a + m] if "lod" in w else None
+    d_lod = None if lod is None else torch.from_numpy(np.ascontiguousarray(lod)).to(dev)
+    C = w["channels"]
+    got = torch.empty((m, C), dtype=torch.float32, device=dev)
+    taps = torch.empty((m, 4), dtype=torch.int32, device=dev)
+    det = torch.empty((m, C), dtype=torch.float32, device=dev)
+    lm = stf.LEVEL_STOCHASTIC if level_mode is None else level_mode
+    p = stf.make_params(filt, seed=2024, level_mode=lm, query_offset=a)
+    stf.stf_lookup_batch(tex.handle, p, d, d_lod, m, got, taps, stream)
+    stf.stf_lookup_batch_deterministic(tex.handle, stf.make_params(filt, level_mode=lm), d, d_lod, m, det,
+                                       stream)
+    torch.cuda.synchronize()
+    got, taps, det = got.cpu().numpy(), taps.cpu().numpy(), det.cpu().numpy()
+    if w["name"] == "dense":
+        ref = textures.Dense3D(np.asarray(w["values"], dtype=np.float64).reshape(w["dims"][::-1]))
+    elif w["name"].startswith("sparse"):
+        sub = touched_leaves(w["origins"], q)
+        ref = textures.Sparse3D(w["origins"][sub], np.asarray(w["values"][sub], dtype=np.float64))
+    elif w["name"] == "neural":
+        ref = textures.Texture2D([np.asarray(p_, dtype=np.float64) for p_ in w["pyramid"]])
+    else:
+        ref = textures.Texture2D([np.asarray(w["values"], dtype=np.float64)])
+    if ref.__class__.__name__ == "Texture2D":
+        rv, rt, ex = filters.lookup_2d(ref, q, lod, filt, stochastic_form=True, level_mode=lm, qid=qid,
+                                       seed=2024)
+        dv, _, _ = filters.lookup_2d(ref, q, lod, filt, stochastic_form=False, level_mode=lm)
+    else:
+        rv, rt, ex = filters.lookup_3d(ref, q, filt, stochastic_form=True, qid=qid, seed=2024)
+        dv, _, _ = filters.lookup_3d(ref, q, filt, stochastic_form=False)
+    same = np.all(taps == rt, axis=1) & ~ex
+    vals = np.asarray(w["pyramid"][0] if w["name"] == "neural" else w["values"], dtype=np.float64)
+    rng = float(vals.max() - vals.min())
+
+    def stats(e):
+        e = np.abs(e)
+        return {"max_abs": float(e.max()), "rms": float(np.sqrt(np.mean(e * e))),
+                "max_rel_to_range": float(e.max() / rng)}
+    return {"stochastic": stats(got[same] - rv[same]), "deterministic": stats(det - dv),
+            "queries": m, "same_taps": int(same.sum()), "value_range": rng,
+            "against": "float64 oracle on the unquantised texels" if w["name"] != "neural"
+                       else "float64 oracle on the target texture the network was trained on"}
+
+
 # ------------------------------------------------------------------ arms
 
 def run_serving(args):
@@ -805,6 +865,7 @@ def run_ours(args):
     value = n * world * args.steps / (total / 1000.0)
 
     extras = {}
+    sparse_extra = []
     if not args.quick:
         variants = [("deterministic_" + filt, deterministic(filt))]
         if w["name"] != "neural":
@@ -891,6 +952,8 @@ def run_ours(args):
         det = extras.get("deterministic_" + filt, {})
         if "lookups_per_s" in det:
             extras["speedup_vs_deterministic"] = value / world / det["lookups_per_s"]
+        if w["name"] == "dense" and world == 1:
+            sparse_extra = sparse_extras(stf, torch, args, extras, stream)
 
     # end to end: pinned host coords -> device, lookup, device -> host each step
     h_coords = torch.from_numpy(w["coords"]).pin_memory()
@@ -989,11 +1052,55 @@ def run_ours(args):
         line["cpu_baseline"] = {"value": rate, "unit": "lookups/s", "cores": cores, "kind": "oracle",
                                 "sample": "first %d queries of the workload, stochastic %s, "
                                           "%.1f s on %d processes" % (ns, filt, dt, cores)}
+        # the same oracle, untimed: the error of the stored texture format
+        line["storage_error_vs_fp64_oracle"] = {w["name"]: storage_error(
+            stf, torch, w, tex, filt, stream, level_mode=level_mode)}
+        for sw, stex in sparse_extra:
+            line["storage_error_vs_fp64_oracle"][sw["name"]] = storage_error(stf, torch, sw, stex, filt, stream)
     print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
     tex.close()
+    for _, stex in sparse_extra:
+        stex.close()
     return 0
+
+
+def sparse_extras(stf, torch, args, extras, stream):
+    """The largest configuration beside the default one: the sparse 2048^3 cloud
+    (FP32 leaves and E4M3 leaves with FP32 leaf scales), 2048x2048 rays x 16 steps
+    (67,108,864 queries), stochastic and deterministic tricubic B-spline, each with
+    its lookups/s, p50/p99 per launch and HBM fraction.  Returns [(workload, texture)]
+    for the storage-error leg."""
+    hbm_peak, _ = peaks()
+    out_list = []
+    base = make_workload("sparse")
+    coords = torch.from_numpy(base["coords"]).cuda()
+    n = coords.shape[0]
+    out = torch.empty((n, 1), dtype=torch.float32, device=coords.device)
+    for name in ("sparse", "sparse_e4m3"):
+        w = dict(base, name=name)
+        T = make_texture(stf, w)
+        ps = stf.make_params("bspline3", seed=2024)
+        pd = stf.make_params("bspline3")
+        sto = lambda: stf.stf_lookup_batch(T.handle, ps, coords, None, n, out, None, stream)
+        det = lambda: stf.stf_lookup_batch_deterministic(T.handle, pd, coords, None, n, out, stream)
+        p1, t1 = time_steps(torch, sto, max(3, args.steps // 2), 2, stream)
+        p2, t2 = time_steps(torch, det, max(3, args.steps // 5), 1, stream)
+        stf.stf_synchronize(T.handle, stream)
+        b = ALGO_BYTES[(name, "stochastic")]
+        v1 = n * len(p1) / (t1 / 1000.0)
+        v2 = n * len(p2) / (t2 / 1000.0)
+        key = "sparse_%s_bspline3" % ("e4m3" if name == "sparse_e4m3" else "fp32")
+        extras[key] = {"workload": "sparse 2048^3 cloud, %d leaves, %s leaves, 2048x2048 rays x 16 steps "
+                                   "(%d queries)" % (len(w["origins"]), TEXEL_FORMAT[name], n),
+                       "lookups_per_s": v1, "ms_p50": pct(p1, 50), "ms_p99": pct(p1, 99),
+                       "hbm_frac": v1 * b / 1e9 / hbm_peak, "algorithmic_bytes_per_lookup": b,
+                       "deterministic_lookups_per_s": v2, "deterministic_ms_p50": pct(p2, 50),
+                       "speedup_vs_deterministic": v1 / v2}
+        out_list.append((w, T))
+    del coords, out
+    return out_list
 
 
 def main():

@@ -182,13 +182,17 @@ typedef struct {
                              other filters */
 } stf_lookup_params;
 
-/* Create a device-resident texture from desc; queued on `stream`, and the call
- * synchronises that stream before returning so that the caller may free its data.
- * Returns STF_ERR_INVALID_ARGUMENT for an inconsistent descriptor,
- * STF_ERR_OUT_OF_MEMORY if device memory runs out (nothing is leaked). */
+/* Create a device-resident texture from desc: the texel function t of Section 2.1
+ * (Eq. 1), non-zero at the discrete texel positions, whose filtered values the
+ * lookups below return (the filter implementations of Appendix B take a texture and a
+ * lookup position).  Queued on `stream`, and the call synchronises that stream before
+ * returning so that the caller may free its data.  Returns STF_ERR_INVALID_ARGUMENT
+ * for an inconsistent descriptor, STF_ERR_OUT_OF_MEMORY if device memory runs out
+ * (nothing is leaked). */
 stf_status stf_create_texture(const stf_texture_desc* desc, void* stream, stf_texture* out);
 
-/* Release a texture and everything it owns.  Waits for work queued on it. */
+/* Release a texture created by stf_create_texture (the texel function of Section 2.1)
+ * and everything it owns.  Waits for work queued on it. */
 stf_status stf_destroy(stf_texture tex);
 
 /* Stochastic filtered lookups (one texel per query; Eq. 3 with the sampling-arrays

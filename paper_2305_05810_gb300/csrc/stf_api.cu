@@ -159,7 +159,9 @@ static stf_status create_grid(stf_texture_s* t, const stf_texture_desc* d, cudaS
     total += (int64_t)w * h * depth;
   }
   const int64_t nvals = total * C;
-  cudaError_t e = dev_alloc(&t->d_texels, (size_t)nvals * es);
+  // 16 bytes of padding: the deterministic dense filter reads rows of four FP16
+  // voxels as aligned 8-byte words, the last of which may extend past the data
+  cudaError_t e = dev_alloc(&t->d_texels, (size_t)nvals * es + 16);
   if (e != cudaSuccess) return fail_cuda(e, "texel allocation");
   t->bytes += nvals * es;
   const cudaMemcpyKind kind = d->data_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;

@@ -300,6 +300,37 @@ __device__ __forceinline__ bool fast_loop(const LookupArgs& a) {
   return a.perm == nullptr && a.taps == nullptr && a.n <= kFastLoopMaxQueries;
 }
 
+// The 3D fast loop takes four consecutive queries per thread when the coordinates and
+// results are 16-byte aligned: its coordinates are then three aligned 16-byte loads
+// and its four results one 16-byte store.  Host and device test the same condition
+// (the host sizes the grid by it).
+__host__ __device__ __forceinline__ bool quad_loop3_ok(const LookupArgs& a) {
+  return a.perm == nullptr && a.taps == nullptr && a.n <= kFastLoopMaxQueries &&
+         (((uintptr_t)a.coords | (uintptr_t)a.out) & 15) == 0;
+}
+
+// Queries 4g .. 4g + 3 for g = thread, thread + stride, ...; the last n mod 4 queries
+// one per thread.  one(x, y, z, j) filters the query with caller's index j.
+template <class One>
+__device__ __forceinline__ void quad_loop3(const LookupArgs& a, One one) {
+  const uint32_t n = (uint32_t)a.n, groups = n >> 2, stride = gridDim.x * blockDim.x;
+  const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
+  const float4* c4 = reinterpret_cast<const float4*>(a.coords);
+  float4* o4 = reinterpret_cast<float4*>(a.out);
+  for (uint32_t g = tid; g < groups; g += stride) {
+    const float4 p = __ldg(c4 + 3 * g), q = __ldg(c4 + 3 * g + 1), r = __ldg(c4 + 3 * g + 2);
+    const uint32_t i = 4 * g;
+    float4 o;
+    o.x = one(p.x, p.y, p.z, i);
+    o.y = one(p.w, q.x, q.y, i + 1);
+    o.z = one(q.z, q.w, r.x, i + 2);
+    o.w = one(r.y, r.z, r.w, i + 3);
+    o4[g] = o;
+  }
+  for (uint32_t i = 4 * groups + tid; i < n; i += stride)
+    a.out[i] = one(__ldg(a.coords + 3 * i), __ldg(a.coords + 3 * i + 1), __ldg(a.coords + 3 * i + 2), i);
+}
+
 __device__ __forceinline__ int64_t query_slot(const LookupArgs& a, int64_t i) {
   return a.perm ? (int64_t)__ldg(a.perm + i) : i;
 }

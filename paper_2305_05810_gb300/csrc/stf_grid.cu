@@ -31,12 +31,11 @@ __device__ __forceinline__ float dense_fetch(const Dense3DView& g, int ix, int i
     return __ldg(reinterpret_cast<const float*>(g.texels) + e);
 }
 
-// One stochastic lookup of query i (caller's index j).  I is int64_t, or uint32_t in
-// the fast loop (3 i + 2 < 2^32 there).
-template <int F, int FMT, bool REUSE, bool OFF32 = false, typename I>
-__device__ __forceinline__ float dense_stochastic_one(const Dense3DView& g, const LookupArgs& a,
-                                                      I i, I j, uint32_t sample, int4& tap) {
-  float x[3] = {__ldg(a.coords + 3 * i), __ldg(a.coords + 3 * i + 1), __ldg(a.coords + 3 * i + 2)};
+// One stochastic lookup at coordinates x (caller's query index j).  J is int64_t, or
+// uint32_t in the fast loops.
+template <int F, int FMT, bool REUSE, bool OFF32 = false, typename J>
+__device__ __forceinline__ float dense_stochastic_at(const Dense3DView& g, const LookupArgs& a,
+                                                     float* x, J j, uint32_t sample, int4& tap) {
   if (!prepare_coords<3>(x)) {
     tap = make_int4(0, 0, 0, -1);
     return g.background;
@@ -68,9 +67,27 @@ __device__ __forceinline__ float dense_stochastic_one(const Dense3DView& g, cons
   }
 }
 
+// One stochastic lookup of query i (caller's index j).  I is int64_t, or uint32_t in
+// the fast loop (3 i + 2 < 2^32 there).
+template <int F, int FMT, bool REUSE, bool OFF32 = false, typename I>
+__device__ __forceinline__ float dense_stochastic_one(const Dense3DView& g, const LookupArgs& a,
+                                                      I i, I j, uint32_t sample, int4& tap) {
+  float x[3] = {__ldg(a.coords + 3 * i), __ldg(a.coords + 3 * i + 1), __ldg(a.coords + 3 * i + 2)};
+  return dense_stochastic_at<F, FMT, REUSE, OFF32>(g, a, x, j, sample, tap);
+}
+
 template <int F, int FMT, bool REUSE>
 __global__ void __launch_bounds__(256) k_dense_stochastic(Dense3DView g, LookupArgs a) {
-  if (fast_loop(a) && (uint64_t)g.nx * (uint64_t)g.ny * (uint64_t)g.nz <= (uint64_t(1) << 32)) {
+  const bool off32 = (uint64_t)g.nx * (uint64_t)g.ny * (uint64_t)g.nz <= (uint64_t(1) << 32);
+  if (off32 && quad_loop3_ok(a)) {
+    quad_loop3(a, [&](float x0, float x1, float x2, uint32_t j) {
+      float x[3] = {x0, x1, x2};
+      int4 tap;
+      return dense_stochastic_at<F, FMT, REUSE, true>(g, a, x, j, a.sample_index, tap);
+    });
+    return;
+  }
+  if (fast_loop(a) && off32) {
     const uint32_t n = (uint32_t)a.n, stride = gridDim.x * blockDim.x;
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
       int4 tap;
@@ -87,10 +104,44 @@ __global__ void __launch_bounds__(256) k_dense_stochastic(Dense3DView g, LookupA
   }
 }
 
+// The T consecutive voxels e .. e + T - 1 of one grid row.  FP16 rows of
+// four come from aligned 8-byte words: one word when e is a multiple of 4, else two
+// (the texel allocation is padded by 16 bytes, so the second word never leaves it),
+// shifted into place.  Other rows are read voxel by voxel.
+template <int FMT, int T>
+__device__ __forceinline__ void dense_row(const void* texels, uint32_t e, float* v) {
+  if constexpr (FMT == STF_FMT_F16 && T == 4) {
+    const uint2* w = reinterpret_cast<const uint2*>(texels) + (e >> 2);
+    const uint32_t s = e & 3;
+    const uint2 a = __ldg(w);
+    uint32_t lo = a.x, hi = a.y;
+    if (s != 0) {
+      const uint2 b = __ldg(w + 1);
+      const uint32_t x0 = s >= 2 ? a.y : a.x, x1 = s >= 2 ? b.x : a.y, x2 = s >= 2 ? b.y : b.x;
+      const uint32_t sh = (s & 1) * 16;
+      lo = __funnelshift_r(x0, x1, sh);
+      hi = __funnelshift_r(x1, x2, sh);
+    }
+    const float2 f0 = __half22float2(*reinterpret_cast<const __half2*>(&lo));
+    const float2 f1 = __half22float2(*reinterpret_cast<const __half2*>(&hi));
+    v[0] = f0.x; v[1] = f0.y; v[2] = f1.x; v[3] = f1.y;
+  } else {
+#pragma unroll
+    for (int k = 0; k < T; ++k) {
+      if constexpr (FMT == STF_FMT_F16)
+        v[k] = __half2float(__ldg(reinterpret_cast<const __half*>(texels) + e + k));
+      else
+        v[k] = __ldg(reinterpret_cast<const float*>(texels) + e + k);
+    }
+  }
+}
+
 template <int F, int FMT>
 __global__ void __launch_bounds__(256) k_dense_deterministic(Dense3DView g, LookupArgs a) {
   using Fl = Filter<F>;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  // grids of at most 2^32 voxels take 32-bit row offsets in the interior path
+  const bool off32 = (uint64_t)g.nx * (uint64_t)g.ny * (uint64_t)g.nz <= (uint64_t(1) << 32);
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += stride) {
     float x[3] = {__ldg(a.coords + 3 * i), __ldg(a.coords + 3 * i + 1), __ldg(a.coords + 3 * i + 2)};
     float acc = g.background;
@@ -108,14 +159,37 @@ __global__ void __launch_bounds__(256) k_dense_deterministic(Dense3DView g, Look
         Fl::weights(fy, wy);
         Fl::weights(fz, wz);
         acc = 0.0f;
+        // (the two-tap filters keep the checked loop: eight scattered voxels gain
+        // nothing from row loads, and measured slower with the extra path)
+        const bool interior = Fl::T == 4 && off32 && bx >= 0 && by >= 0 && bz >= 0 &&
+                              bx + Fl::T <= g.nx && by + Fl::T <= g.ny && bz + Fl::T <= g.nz;
+        if (interior) {
+          // the whole window inside the grid: rows of T voxels along x, no bounds tests;
+          // each row's weighted sum, then the rows weighted by wy * wz
+          const uint32_t nx = (uint32_t)g.nx, ny = (uint32_t)g.ny;
+          const uint32_t e0 = ((uint32_t)bz * ny + (uint32_t)by) * nx + (uint32_t)bx;
 #pragma unroll
-        for (int kz = 0; kz < Fl::T; ++kz) {
+          for (int kz = 0; kz < Fl::T; ++kz) {
 #pragma unroll
-          for (int ky = 0; ky < Fl::T; ++ky) {
-            const float wyz = wy[ky] * wz[kz];
+            for (int ky = 0; ky < Fl::T; ++ky) {
+              float v[Fl::T];
+              dense_row<FMT, Fl::T>(g.texels, e0 + ((uint32_t)kz * ny + (uint32_t)ky) * nx, v);
+              float r = wx[0] * v[0];
 #pragma unroll
-            for (int kx = 0; kx < Fl::T; ++kx)
-              acc = fmaf(wx[kx] * wyz, dense_fetch<FMT>(g, bx + kx, by + ky, bz + kz), acc);
+              for (int kx = 1; kx < Fl::T; ++kx) r = fmaf(wx[kx], v[kx], r);
+              acc = fmaf(wy[ky] * wz[kz], r, acc);
+            }
+          }
+        } else {
+#pragma unroll
+          for (int kz = 0; kz < Fl::T; ++kz) {
+#pragma unroll
+            for (int ky = 0; ky < Fl::T; ++ky) {
+              const float wyz = wy[ky] * wz[kz];
+#pragma unroll
+              for (int kx = 0; kx < Fl::T; ++kx)
+                acc = fmaf(wx[kx] * wyz, dense_fetch<FMT>(g, bx + kx, by + ky, bz + kz), acc);
+            }
           }
         }
       }
@@ -153,7 +227,9 @@ cudaError_t launch_tex2d(Op op, int filter, int fmt, int channels, const Tex2DVi
 template <int F, int FMT>
 static cudaError_t run_dense(Op op, const Dense3DView& g, const LookupArgs& a, cudaStream_t s) {
   const int threads = 256;
-  const int blocks = grid_blocks(a.n, threads, op == OP_STOCHASTIC ? kStochasticWaves : 4);
+  // the four-query loop needs a quarter of the threads
+  const int64_t units = (op == OP_STOCHASTIC && quad_loop3_ok(a)) ? (a.n + 3) / 4 : a.n;
+  const int blocks = grid_blocks(units, threads, op == OP_STOCHASTIC ? kStochasticWaves : 4);
   if (op == OP_STOCHASTIC) {
     if constexpr (UsesReuse<F>::value) {
       if (a.reuse) k_dense_stochastic<F, FMT, true><<<blocks, threads, 0, s>>>(g, a);

@@ -296,13 +296,12 @@ __device__ __forceinline__ void stage_upper(const SparseDev& g, UpperSmem& su) {
   __syncthreads();
 }
 
-// One stochastic lookup of query i (caller's index j).  I is int64_t, or uint32_t in
-// the fast loop (3 i + 2 < 2^32 there).
-template <int F, int FMT, bool REUSE, typename I>
-__device__ __forceinline__ float sparse_stochastic_one(const SparseDev& g, const UpperSmem& su,
-                                                       const LookupArgs& a, I i, I j,
-                                                       uint32_t sample, int4& tap) {
-  float x[3] = {__ldg(a.coords + 3 * i), __ldg(a.coords + 3 * i + 1), __ldg(a.coords + 3 * i + 2)};
+// One stochastic lookup at coordinates x (caller's query index j).  J is int64_t, or
+// uint32_t in the fast loops.
+template <int F, int FMT, bool REUSE, typename J>
+__device__ __forceinline__ float sparse_stochastic_at(const SparseDev& g, const UpperSmem& su,
+                                                      const LookupArgs& a, float* x, J j,
+                                                      uint32_t sample, int4& tap) {
   if (!prepare_coords<3>(x)) {
     tap = make_int4(0, 0, 0, -1);
     return g.background;
@@ -335,10 +334,28 @@ __device__ __forceinline__ float sparse_stochastic_one(const SparseDev& g, const
   }
 }
 
+// One stochastic lookup of query i (caller's index j).  I is int64_t, or uint32_t in
+// the fast loop (3 i + 2 < 2^32 there).
+template <int F, int FMT, bool REUSE, typename I>
+__device__ __forceinline__ float sparse_stochastic_one(const SparseDev& g, const UpperSmem& su,
+                                                       const LookupArgs& a, I i, I j,
+                                                       uint32_t sample, int4& tap) {
+  float x[3] = {__ldg(a.coords + 3 * i), __ldg(a.coords + 3 * i + 1), __ldg(a.coords + 3 * i + 2)};
+  return sparse_stochastic_at<F, FMT, REUSE>(g, su, a, x, j, sample, tap);
+}
+
 template <int F, int FMT, bool REUSE>
 __global__ void __launch_bounds__(256) k_sparse_stochastic(SparseDev g, LookupArgs a) {
   __shared__ UpperSmem su;
   stage_upper(g, su);
+  if (quad_loop3_ok(a)) {
+    quad_loop3(a, [&](float x0, float x1, float x2, uint32_t j) {
+      float x[3] = {x0, x1, x2};
+      int4 tap;
+      return sparse_stochastic_at<F, FMT, REUSE>(g, su, a, x, j, a.sample_index, tap);
+    });
+    return;
+  }
   if (fast_loop(a)) {
     const uint32_t n = (uint32_t)a.n, stride = gridDim.x * blockDim.x;
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
@@ -434,7 +451,9 @@ __global__ void __launch_bounds__(256) k_sparse_accumulate(SparseDev g, LookupAr
 template <int F, int FMT>
 static cudaError_t run_sparse(Op op, const SparseDev& g, const LookupArgs& a, cudaStream_t s) {
   const int threads = 256;
-  const int blocks = grid_blocks(a.n, threads, op == OP_STOCHASTIC ? kStochasticWaves : 4);
+  // the four-query loop needs a quarter of the threads
+  const int64_t units = (op == OP_STOCHASTIC && quad_loop3_ok(a)) ? (a.n + 3) / 4 : a.n;
+  const int blocks = grid_blocks(units, threads, op == OP_STOCHASTIC ? kStochasticWaves : 4);
   if (op == OP_STOCHASTIC) {
     if constexpr (UsesReuse<F>::value) {
       if (a.reuse) k_sparse_stochastic<F, FMT, true><<<blocks, threads, 0, s>>>(g, a);

@@ -1,8 +1,11 @@
 """The stochastic kernels of dense, sparse and 2D textures run calls that ask for no tap
 output and no binning on 32-bit indices (a loop of their own, with 32-bit voxel offsets
-on dense grids).  The parity tests check the general loop against the oracle with tap
-output on; here the same calls without tap output must give bit-identical results, for
-every filter, on inputs that include NaN, huge and out-of-range coordinates."""
+on dense grids); on 3D grids with 16-byte aligned coordinates and results that loop
+takes four consecutive queries per thread (three 16-byte coordinate loads, one 16-byte
+result store), otherwise one.  The parity tests check the general loop against the
+oracle with tap output on; here the same calls without tap output must give
+bit-identical results, for every filter, on inputs that include NaN, huge and
+out-of-range coordinates, with a ragged tail (n mod 4 != 0) and misaligned views."""
 import numpy as np
 import pytest
 import torch
@@ -42,6 +45,35 @@ def _same(T, q, lod=None, **params):
 def _params(filt):
     return {"filter": filt, "seed": 99, "sample_index": 3, "query_offset": 12345,
             "width": 0.9 if filt == "fis_gaussian" else 0.0}
+
+
+def _same_3d_views(T, q, **params):
+    """Aligned (four queries per thread), misaligned by one query (one per thread) and
+    the general loop with tap output: bit-equal on the common queries."""
+    n = q.shape[0]
+    taps = torch.empty((n, 4), dtype=torch.int32, device=dev())
+    general = T.lookup(q, taps=taps, **params)
+    quad = T.lookup(q, **params)
+    p1 = dict(params, query_offset=params["query_offset"] + 1)
+    out1 = torch.empty((n, 1), dtype=torch.float32, device=dev())
+    stf.stf_lookup_batch(T.handle, stf.make_params(**p1), q[1:], None, n - 1, out1[1:])  # 12-byte offset
+    torch.cuda.synchronize()
+    assert q.shape[0] % 4 != 0 and q[1:].data_ptr() % 16 != 0
+    torch.testing.assert_close(quad, general, rtol=0, atol=0, equal_nan=True)
+    torch.testing.assert_close(out1[1:], general[1:], rtol=0, atol=0, equal_nan=True)
+
+
+@pytest.mark.parametrize("filt", ["linear", "bspline3", "catmull_rom", "catmull_rom_positivized"])
+def test_dense_and_sparse_quad_loop_views(filt):
+    vals = synth.dense_density(n=40, seed=6, period=9.0)
+    T = stf.Texture(stf.KIND_DENSE3D, vals, dims=(40, 40, 40), fmt=stf.FMT_F16)
+    q = (synth.uniform(3 * 70001, 8).reshape(-1, 3) * np.float32(48) - np.float32(4)).astype(np.float32)
+    _same_3d_views(T, to_dev(np.concatenate([q, _edge(3)])), **_params(filt))
+    origins, values = synth.sparse_cloud(domain=512, seed=9)
+    S = stf.Texture(stf.KIND_SPARSE3D, values, fmt=stf.FMT_E4M3_SCALED, leaf_origins=origins)
+    o = origins[np.arange(30001) % len(origins)].astype(np.float32)
+    q = (o + synth.uniform(3 * 30001, 10).reshape(-1, 3) * np.float32(10) - np.float32(1)).astype(np.float32)
+    _same_3d_views(S, to_dev(np.concatenate([q, _edge(3)])), **_params(filt))
 
 
 @pytest.mark.parametrize("fmt", [stf.FMT_F32, stf.FMT_F16])
