@@ -900,17 +900,34 @@ def run_ours(args):
                           tex.handle, pshuf, shuffled, lod_shuf, n, out, None, stream)),
                      ("stochastic_shuffled_binned", lambda: stf.stf_lookup_batch(
                           tex.handle, pshuf_b, shuffled, lod_shuf, n, out, None, stream))]
+        if w["name"] == "dense" and filt in ("bspline3", "linear"):
+            # the queries whose filter window touches the grid (the others return the
+            # background without drawing): the same kernel on those alone
+            lo, hi = (-1, 2) if filt == "bspline3" else (0, 1)
+            fl = torch.floor(coords)
+            dims = torch.tensor(w["dims"], device=dev, dtype=coords.dtype)
+            hit = ((fl + hi >= 0) & (fl + lo < dims)).all(dim=1)
+            hits = coords[hit].contiguous()
+            nh = hits.shape[0]
+            ph = stf.make_params(filt, seed=2024, level_mode=level_mode, query_offset=qoff)
+            variants += [("stochastic_hits_only", lambda: stf.stf_lookup_batch(
+                tex.handle, ph, hits, None, nh, out, None, stream))]
         hbm_peak, _ = peaks()
         for name, fn in variants:
             try:
                 p2, t2 = time_steps(torch, fn, max(3, args.steps // 2), 2, stream)
                 nq = min(n, 1 << 20) if name.endswith("first_2^20") else n
+                if name == "stochastic_hits_only":
+                    nq = nh
                 extras[name] = {"lookups_per_s": nq * len(p2) / (t2 / 1000.0),
                                 "ms_p50": pct(p2, 50), "ms_p99": pct(p2, 99)}
                 b = stochastic_extra_bytes(w["name"], name)
                 if b is not None:
                     extras[name]["hbm_frac"] = extras[name]["lookups_per_s"] * b / 1e9 / hbm_peak
                     extras[name]["algorithmic_bytes_per_lookup"] = b
+                if name == "stochastic_hits_only":
+                    extras[name]["queries"] = nh
+                    extras[name]["fraction_of_workload"] = nh / n
             except stf.StfError as e:
                 extras[name] = {"unavailable": str(e)}
         if w["name"] == "sparse_e4m3":
@@ -1039,7 +1056,9 @@ def run_ours(args):
         tflops = flops * n / (avg_launch_ms / 1000.0) / 1e12
         line["roofline_tensor"] = {"bound": "tensor", "achieved": tflops, "peak": bf16_peak(),
                                    "unit": "TFLOP/s", "frac": tflops / bf16_peak(),
-                                   "flops_per_lookup": flops, "path": "mma.sync fp16, fp32 accumulate"}
+                                   "flops_per_lookup": flops,
+                                   "path": "tcgen05.mma kind::f16 (M = 128, binary16 operands, float32 "
+                                           "accumulators in tensor memory)"}
         line["config"]["train"] = {"steps": args.train_steps, "batch": 1 << 16,
                                    "loss_first_last": w.get("train_loss")}
         line["config"]["level_mode"] = "nearest (one decode vs four)"
@@ -1057,6 +1076,11 @@ def run_ours(args):
             stf, torch, w, tex, filt, stream, level_mode=level_mode)}
         for sw, stex in sparse_extra:
             line["storage_error_vs_fp64_oracle"][sw["name"]] = storage_error(stf, torch, sw, stex, filt, stream)
+        if w["name"] == "tex2d":
+            # the same 2D texture stored in FP16
+            t16 = stf.Texture(stf.KIND_TEX2D, w["values"], dims=w["dims"], channels=4, fmt=stf.FMT_F16)
+            line["storage_error_vs_fp64_oracle"]["tex2d_fp16"] = storage_error(stf, torch, w, t16, filt, stream)
+            t16.close()
     print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
@@ -1078,6 +1102,13 @@ def sparse_extras(stf, torch, args, extras, stream):
     coords = torch.from_numpy(base["coords"]).cuda()
     n = coords.shape[0]
     out = torch.empty((n, 1), dtype=torch.float32, device=coords.device)
+    # the queries whose B-spline window touches the active leaves' bounding box
+    blo = torch.tensor(base["origins"].min(axis=0), device=coords.device, dtype=coords.dtype)
+    bhi = torch.tensor(base["origins"].max(axis=0) + 8, device=coords.device, dtype=coords.dtype)
+    fl = torch.floor(coords)
+    hits = coords[((fl + 2 >= blo) & (fl - 1 < bhi)).all(dim=1)].contiguous()
+    nh = hits.shape[0]
+    del fl
     for name in ("sparse", "sparse_e4m3"):
         w = dict(base, name=name)
         T = make_texture(stf, w)
@@ -1087,6 +1118,8 @@ def sparse_extras(stf, torch, args, extras, stream):
         det = lambda: stf.stf_lookup_batch_deterministic(T.handle, pd, coords, None, n, out, stream)
         p1, t1 = time_steps(torch, sto, max(3, args.steps // 2), 2, stream)
         p2, t2 = time_steps(torch, det, max(3, args.steps // 5), 1, stream)
+        hit = lambda: stf.stf_lookup_batch(T.handle, ps, hits, None, nh, out, None, stream)
+        p3, t3 = time_steps(torch, hit, max(3, args.steps // 2), 2, stream)
         stf.stf_synchronize(T.handle, stream)
         b = ALGO_BYTES[(name, "stochastic")]
         v1 = n * len(p1) / (t1 / 1000.0)
@@ -1097,9 +1130,12 @@ def sparse_extras(stf, torch, args, extras, stream):
                        "lookups_per_s": v1, "ms_p50": pct(p1, 50), "ms_p99": pct(p1, 99),
                        "hbm_frac": v1 * b / 1e9 / hbm_peak, "algorithmic_bytes_per_lookup": b,
                        "deterministic_lookups_per_s": v2, "deterministic_ms_p50": pct(p2, 50),
-                       "speedup_vs_deterministic": v1 / v2}
+                       "speedup_vs_deterministic": v1 / v2,
+                       "hits_only": {"queries": nh, "fraction_of_workload": nh / n,
+                                     "lookups_per_s": nh * len(p3) / (t3 / 1000.0),
+                                     "hbm_frac": nh * len(p3) / (t3 / 1000.0) * b / 1e9 / hbm_peak}}
         out_list.append((w, T))
-    del coords, out
+    del coords, out, hits
     return out_list
 
 

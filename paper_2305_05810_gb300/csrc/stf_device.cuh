@@ -248,6 +248,40 @@ __device__ __forceinline__ float pick_taps_r(const float* x, const uint4& r, int
   }
 }
 
+// ---------------------------------------------------------------- misses
+// Filters whose estimate is the fetched texel itself, drawn from the fixed window
+// floor(x) + LO .. floor(x) + HI on every axis: the tent and the cubic B-spline, as
+// discrete taps or by filter importance sampling (a sum of 1 or 3 uniforms on
+// [-1/2, 1/2) keeps floor(x + s + 1/2) in the same window).  When that window lies
+// outside the region that holds texels on some axis, every tap the draw can reach reads
+// the background, so the lookup returns it without drawing (the same value).
+template <int F> struct FixedWindow { static constexpr bool value = false; static constexpr int LO = 0, HI = 0; };
+template <> struct FixedWindow<STF_FILTER_LINEAR> { static constexpr bool value = true; static constexpr int LO = 0, HI = 1; };
+template <> struct FixedWindow<STF_FILTER_BSPLINE3> { static constexpr bool value = true; static constexpr int LO = -1, HI = 2; };
+template <> struct FixedWindow<STF_FILTER_FIS_LINEAR> { static constexpr bool value = true; static constexpr int LO = 0, HI = 1; };
+template <> struct FixedWindow<STF_FILTER_FIS_BSPLINE3> { static constexpr bool value = true; static constexpr int LO = -1, HI = 2; };
+
+// The window misses [lo, hi) on an axis iff floor(x) + HI < lo or floor(x) + LO >= hi,
+// that is x < lo - HI or x >= hi - LO for the integers lo - HI and hi - LO; compared
+// with these integers rounded up to float32 both tests stay exact.
+struct MissBox {
+  float lo[3], hi[3];
+};
+
+template <int F>
+__device__ __forceinline__ MissBox miss_box(int lx, int ly, int lz, int hx, int hy, int hz) {
+  using W = FixedWindow<F>;
+  MissBox m;
+  m.lo[0] = __int2float_ru(lx - W::HI); m.lo[1] = __int2float_ru(ly - W::HI); m.lo[2] = __int2float_ru(lz - W::HI);
+  m.hi[0] = __int2float_ru(hx - W::LO); m.hi[1] = __int2float_ru(hy - W::LO); m.hi[2] = __int2float_ru(hz - W::LO);
+  return m;
+}
+
+__device__ __forceinline__ bool misses(const MissBox& m, const float* x) {
+  return x[0] < m.lo[0] || x[0] >= m.hi[0] || x[1] < m.lo[1] || x[1] >= m.hi[1] || x[2] < m.lo[2] ||
+         x[2] >= m.hi[2];
+}
+
 // ---------------------------------------------------------------- views
 struct Tex2DView {
   const void* texels;     // storage format, [level][y][x][c]; DCT6: [level][by][bx][c] words

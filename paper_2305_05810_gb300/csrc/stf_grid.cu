@@ -32,13 +32,19 @@ __device__ __forceinline__ float dense_fetch(const Dense3DView& g, int ix, int i
 }
 
 // One stochastic lookup at coordinates x (caller's query index j).  J is int64_t, or
-// uint32_t in the fast loops.
+// uint32_t in the fast loops.  With a miss box (the fast loops, which write no tap
+// output), a fixed-window filter whose window lies outside the grid returns the
+// background without drawing.
 template <int F, int FMT, bool REUSE, bool OFF32 = false, typename J>
 __device__ __forceinline__ float dense_stochastic_at(const Dense3DView& g, const LookupArgs& a,
-                                                     float* x, J j, uint32_t sample, int4& tap) {
+                                                     float* x, J j, uint32_t sample, int4& tap,
+                                                     const MissBox* miss = nullptr) {
   if (!prepare_coords<3>(x)) {
     tap = make_int4(0, 0, 0, -1);
     return g.background;
+  }
+  if constexpr (FixedWindow<F>::value) {
+    if (miss && misses(*miss, x)) return g.background;
   }
   const uint4 r = query_variates(a, j, sample);
   if constexpr (IsFis<F>::value) {
@@ -79,19 +85,21 @@ __device__ __forceinline__ float dense_stochastic_one(const Dense3DView& g, cons
 template <int F, int FMT, bool REUSE>
 __global__ void __launch_bounds__(256) k_dense_stochastic(Dense3DView g, LookupArgs a) {
   const bool off32 = (uint64_t)g.nx * (uint64_t)g.ny * (uint64_t)g.nz <= (uint64_t(1) << 32);
+  const MissBox mb = miss_box<F>(0, 0, 0, g.nx, g.ny, g.nz);
   if (off32 && quad_loop3_ok(a)) {
     quad_loop3(a, [&](float x0, float x1, float x2, uint32_t j) {
       float x[3] = {x0, x1, x2};
       int4 tap;
-      return dense_stochastic_at<F, FMT, REUSE, true>(g, a, x, j, a.sample_index, tap);
+      return dense_stochastic_at<F, FMT, REUSE, true>(g, a, x, j, a.sample_index, tap, &mb);
     });
     return;
   }
   if (fast_loop(a) && off32) {
     const uint32_t n = (uint32_t)a.n, stride = gridDim.x * blockDim.x;
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+      float x[3] = {__ldg(a.coords + 3 * i), __ldg(a.coords + 3 * i + 1), __ldg(a.coords + 3 * i + 2)};
       int4 tap;
-      a.out[i] = dense_stochastic_one<F, FMT, REUSE, true>(g, a, i, i, a.sample_index, tap);
+      a.out[i] = dense_stochastic_at<F, FMT, REUSE, true>(g, a, x, i, a.sample_index, tap, &mb);
     }
     return;
   }
@@ -159,11 +167,17 @@ __global__ void __launch_bounds__(256) k_dense_deterministic(Dense3DView g, Look
         Fl::weights(fy, wy);
         Fl::weights(fz, wz);
         acc = 0.0f;
+        // a window entirely outside the grid on some axis reads only the background,
+        // and the weights sum to one (partition of unity)
+        const bool outside = bx + Fl::T <= 0 || by + Fl::T <= 0 || bz + Fl::T <= 0 || bx >= g.nx ||
+                             by >= g.ny || bz >= g.nz;
         // (the two-tap filters keep the checked loop: eight scattered voxels gain
         // nothing from row loads, and measured slower with the extra path)
         const bool interior = Fl::T == 4 && off32 && bx >= 0 && by >= 0 && bz >= 0 &&
                               bx + Fl::T <= g.nx && by + Fl::T <= g.ny && bz + Fl::T <= g.nz;
-        if (interior) {
+        if (outside) {
+          acc = g.background;
+        } else if (interior) {
           // the whole window inside the grid: rows of T voxels along x, no bounds tests;
           // each row's weighted sum, then the rows weighted by wy * wz
           const uint32_t nx = (uint32_t)g.nx, ny = (uint32_t)g.ny;

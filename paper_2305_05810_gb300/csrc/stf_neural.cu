@@ -1,5 +1,5 @@
 // Neural textures: latent MIP levels decoded by an 8 -> 64 -> 64 -> 7 ReLU MLP on
-// the tensor cores (mma.sync m16n8k16, binary16 operands, float32 accumulation).
+// the tensor cores (binary16 operands, float32 accumulation).
 //
 // The paper motivates stochastic filtering for decoders that are expensive to run
 // per texel, neural texture representations among them (Section 1; Section 5.2,
@@ -7,15 +7,10 @@
 // inverse-CDF tap choice as a plain 2D texture and decodes it once; the
 // deterministic lookup decodes every tap and filters the decoded values.
 //
-// MMA data flow: a warp owns 16-row tiles (queries or training texels).  The float32
-// accumulator fragment of two adjacent 8-column output tiles has exactly the
-// register layout of a 16-wide binary16 A fragment, so each layer's ReLU output is
-// packed in registers and fed to the next layer without a trip through shared
-// memory.  Weight B fragments are read from shared-memory images laid out so that
-// every fragment register is one aligned 32-bit word (rows padded to avoid bank
-// conflicts).  The weight gradients H^T G reduce over the batch, which is the K
-// dimension of that product; their fragments come from row-major activation tiles
-// through ldmatrix.trans.
+// The stochastic and the deterministic decode and the training (forward, backward and
+// weight gradients) run on the fifth-generation tensor cores: tcgen05.mma on 128-row
+// tiles, operands in shared memory, accumulators in tensor memory (see the tcgen05
+// sections below).
 #include <cstddef>
 #include <math.h>
 
@@ -33,21 +28,12 @@ static_assert(NPARAM == 5191, "parameter count");
 // w3t[8][72] = W3^T (row 7 zero); backward: w2r[64][72] = W2, w3r[64][8] = W3 (col 7
 // zero), w1r[8][72] = W1.
 constexpr int I_W1T = 0, I_W2T = 1536, I_W3T = 6144, I_W2R = 6720, I_W3R = 11328, I_W1R = 11840;
-constexpr int IMG_FWD = 6720, IMG_ALL = 12416;
+constexpr int IMG_ALL = 12416;
 constexpr int NBIAS = 136;   // b1[64], b2[64], b3[8] (b3[7] = 0)
-constexpr int S24 = 12, S72 = 36, S8 = 4;   // row strides in 32-bit words
 
 }  // namespace nn
 
-// ---------------------------------------------------------------- MMA helpers
-
-__device__ __forceinline__ void mma16816(float* d, const uint32_t* a, uint32_t b0, uint32_t b1) {
-  asm volatile(
-      "mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
-      "{%8,%9}, {%0,%1,%2,%3};\n"
-      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
-}
+// ---------------------------------------------------------------- binary16 pairs
 
 __device__ __forceinline__ uint32_t pack_h2(float lo, float hi) {
   const __half2 h = __floats2half2_rn(lo, hi);
@@ -56,103 +42,6 @@ __device__ __forceinline__ uint32_t pack_h2(float lo, float hi) {
 
 __device__ __forceinline__ float2 unpack_h2(uint32_t w) {
   return __half22float2(*reinterpret_cast<const __half2*>(&w));
-}
-
-__device__ __forceinline__ void ldsm_x4_trans(uint32_t* r, const void* p) {
-  const uint32_t a = (uint32_t)__cvta_generic_to_shared(p);
-  asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];\n"
-               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
-               : "r"(a));
-}
-
-__device__ __forceinline__ void ldsm_x2_trans(uint32_t* r, const void* p) {
-  const uint32_t a = (uint32_t)__cvta_generic_to_shared(p);
-  asm volatile("ldmatrix.sync.aligned.m8n8.x2.trans.shared.b16 {%0,%1}, [%2];\n"
-               : "=r"(r[0]), "=r"(r[1])
-               : "r"(a));
-}
-
-// Copy the weight images and biases into shared memory (whole CTA).
-__device__ __forceinline__ void stage_weights(const NeuralDev& nd, uint32_t* sW, float* sB, int words) {
-  const uint32_t* src = reinterpret_cast<const uint32_t*>(nd.wimg);
-  for (int k = threadIdx.x; k < words; k += blockDim.x) sW[k] = __ldg(src + k);
-  for (int k = threadIdx.x; k < nn::NBIAS; k += blockDim.x) sB[k] = __ldg(nd.bias + k);
-  __syncthreads();
-}
-
-// Forward pass of MT 16-row tiles.  sA: the warp's 32 input rows, 4 words (8 halves)
-// per row; rows 16*mt .. 16*mt + 15 form tile mt.  Y rows go to sY (8 floats per
-// row, column 7 is padding).  When H1/H2 pointers are given the tiles' hidden
-// activations (binary16) are kept for the caller in a2/a3.
-template <int MT>
-__device__ __forceinline__ void mlp_forward(const uint32_t* sW, const float* sB, const uint32_t* sA,
-                                            int row0, float (*sY)[8], uint32_t (*a2)[4][4],
-                                            uint32_t (*a3)[4][4]) {
-  const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
-  uint32_t a1[MT][4];
-#pragma unroll
-  for (int m = 0; m < MT; ++m) {
-    a1[m][0] = sA[(row0 + 16 * m + g) * 4 + t];
-    a1[m][1] = sA[(row0 + 16 * m + g + 8) * 4 + t];
-    a1[m][2] = 0u;
-    a1[m][3] = 0u;
-  }
-  const uint32_t* w1t = sW + nn::I_W1T / 2;
-  const uint32_t* w2t = sW + nn::I_W2T / 2;
-  const uint32_t* w3t = sW + nn::I_W3T / 2;
-#pragma unroll
-  for (int j = 0; j < 8; ++j) {
-    const uint32_t b0 = w1t[(8 * j + g) * nn::S24 + t];
-    const float bl = sB[8 * j + 2 * t], bh = sB[8 * j + 2 * t + 1];
-#pragma unroll
-    for (int m = 0; m < MT; ++m) {
-      float c[4] = {bl, bh, bl, bh};
-      mma16816(c, a1[m], b0, 0u);
-      a2[m][j >> 1][(j & 1) * 2 + 0] = pack_h2(fmaxf(c[0], 0.f), fmaxf(c[1], 0.f));
-      a2[m][j >> 1][(j & 1) * 2 + 1] = pack_h2(fmaxf(c[2], 0.f), fmaxf(c[3], 0.f));
-    }
-  }
-#pragma unroll
-  for (int j = 0; j < 8; ++j) {
-    const float bl = sB[64 + 8 * j + 2 * t], bh = sB[64 + 8 * j + 2 * t + 1];
-    float c[MT][4];
-#pragma unroll
-    for (int m = 0; m < MT; ++m) {
-      c[m][0] = bl; c[m][1] = bh; c[m][2] = bl; c[m][3] = bh;
-    }
-#pragma unroll
-    for (int kc = 0; kc < 4; ++kc) {
-      const uint32_t b0 = w2t[(8 * j + g) * nn::S72 + 8 * kc + t];
-      const uint32_t b1 = w2t[(8 * j + g) * nn::S72 + 8 * kc + 4 + t];
-#pragma unroll
-      for (int m = 0; m < MT; ++m) mma16816(c[m], a2[m][kc], b0, b1);
-    }
-#pragma unroll
-    for (int m = 0; m < MT; ++m) {
-      a3[m][j >> 1][(j & 1) * 2 + 0] = pack_h2(fmaxf(c[m][0], 0.f), fmaxf(c[m][1], 0.f));
-      a3[m][j >> 1][(j & 1) * 2 + 1] = pack_h2(fmaxf(c[m][2], 0.f), fmaxf(c[m][3], 0.f));
-    }
-  }
-  float c[MT][4];
-  const float bl = sB[128 + 2 * t], bh = sB[128 + 2 * t + 1];
-#pragma unroll
-  for (int m = 0; m < MT; ++m) {
-    c[m][0] = bl; c[m][1] = bh; c[m][2] = bl; c[m][3] = bh;
-  }
-#pragma unroll
-  for (int kc = 0; kc < 4; ++kc) {
-    const uint32_t b0 = w3t[g * nn::S72 + 8 * kc + t];
-    const uint32_t b1 = w3t[g * nn::S72 + 8 * kc + 4 + t];
-#pragma unroll
-    for (int m = 0; m < MT; ++m) mma16816(c[m], a3[m][kc], b0, b1);
-  }
-#pragma unroll
-  for (int m = 0; m < MT; ++m) {
-    sY[row0 + 16 * m + g][2 * t] = c[m][0];
-    sY[row0 + 16 * m + g][2 * t + 1] = c[m][1];
-    sY[row0 + 16 * m + g + 8][2 * t] = c[m][2];
-    sY[row0 + 16 * m + g + 8][2 * t + 1] = c[m][3];
-  }
 }
 
 // ---------------------------------------------------------------- lookups
@@ -166,12 +55,6 @@ __device__ __forceinline__ uint4 neural_texel(const NeuralDev& nd, int L, int x,
   return __ldg(reinterpret_cast<const uint4*>(base + (nd.lvl_off[L] + (int64_t)cy * w + cx) * 8));
 }
 
-struct NeuralSmem {
-  uint32_t w[nn::IMG_ALL / 2];
-  float b[nn::NBIAS];
-  uint32_t a[4][32 * 4];   // per warp: 32 rows x 8 halves
-  float y[4][32][8];       // per warp: 32 rows x 8 floats
-};
 
 __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
   const uint32_t d = (uint32_t)__cvta_generic_to_shared(smem);
@@ -321,6 +204,46 @@ __device__ __forceinline__ void tmem_ld<8>(uint32_t taddr, uint32_t* r) {
   asm volatile("tcgen05.wait::ld.sync.aligned;");
 }
 
+// The forward weights as K-major no-swizzle B tiles (threads tid, tid + nt, ...):
+// W1^T (64 x 16) with its bias split into binary16 (hi, lo) in k 8, 9; W2^T (64 x 64);
+// W3^T (16 x 64, rows >= 7 zero); the b2 and b3 bias chunks (64 x 16, 16 x 16) with
+// (hi, lo) in k 0, 1; and one 8-row group of ones in columns 0, 1.  A bias b enters the
+// accumulator as b_hi + b_lo, b_hi = fp16(b), b_lo = fp16(b - b_hi): to about 2^-22 |b|.
+__device__ __forceinline__ void stage_fwd_weights(const NeuralDev& nd, unsigned char* b1, unsigned char* b2,
+                                                  unsigned char* b3, unsigned char* b2x, unsigned char* b3x,
+                                                  unsigned char* ones, int tid, int nt) {
+  const uint4* img = reinterpret_cast<const uint4*>(nd.wimg);
+  auto split = [](float b) -> uint32_t {
+    const __half hi = __float2half_rn(b);
+    const __half lo = __float2half_rn(b - __half2float(hi));
+    return (uint32_t)__half_as_ushort(hi) | ((uint32_t)__half_as_ushort(lo) << 16);
+  };
+  const uint4 z = make_uint4(0, 0, 0, 0);
+  for (int n = tid; n < 64; n += nt) {
+    *reinterpret_cast<uint4*>(b1 + off(n, 0, 16)) = __ldg(img + (nn::I_W1T + n * 24) / 8);
+    *reinterpret_cast<uint4*>(b1 + off(n, 8, 16)) = make_uint4(split(__ldg(nd.bias + n)), 0, 0, 0);
+    *reinterpret_cast<uint4*>(b2x + off(n, 0, 16)) = make_uint4(split(__ldg(nd.bias + 64 + n)), 0, 0, 0);
+    *reinterpret_cast<uint4*>(b2x + off(n, 8, 16)) = z;
+  }
+  for (int n = tid; n < 16; n += nt) {
+    const uint32_t b = n < 7 ? split(__ldg(nd.bias + 128 + n)) : 0u;
+    *reinterpret_cast<uint4*>(b3x + off(n, 0, 16)) = make_uint4(b, 0, 0, 0);
+    *reinterpret_cast<uint4*>(b3x + off(n, 8, 16)) = z;
+  }
+  for (int r = tid; r < 8; r += nt) {
+    *reinterpret_cast<uint4*>(ones + off(r, 0, 16)) = make_uint4(0x3C003C00u, 0, 0, 0);
+    *reinterpret_cast<uint4*>(ones + off(r, 8, 16)) = z;
+  }
+  for (int e = tid; e < 64 * 8; e += nt) {
+    const int n = e >> 3, kc = e & 7;
+    *reinterpret_cast<uint4*>(b2 + off(n, 8 * kc, 64)) = __ldg(img + (nn::I_W2T + n * 72 + 8 * kc) / 8);
+  }
+  for (int e = tid; e < 16 * 8; e += nt) {
+    const int n = e >> 3, kc = e & 7;
+    *reinterpret_cast<uint4*>(b3 + off(n, 8 * kc, 64)) = n < 8 ? __ldg(img + (nn::I_W3T + n * 72 + 8 * kc) / 8) : z;
+  }
+}
+
 struct Group {                       // one tile in flight
   unsigned char a1[A1_BYTES];
   unsigned char a2[A2_BYTES];          // H1, then H2, then the staged output rows
@@ -386,39 +309,7 @@ __global__ void __launch_bounds__(256, 4) k_neural_stochastic_tc(NeuralDev nd, L
   tc::Group& G = s.grp[g];
   // weights: binary16 images -> K-major no-swizzle B tiles (16-byte rows)
   {
-    const uint4* img = reinterpret_cast<const uint4*>(nd.wimg);
-    // Biases enter the MMAs as an extra K chunk: a bias b is split into binary16
-    // b_hi = fp16(b) and b_lo = fp16(b - b_hi), multiplied by two columns of ones, so
-    // the float32 accumulator receives b to about 2^-22 |b|.
-    auto split = [](float b) -> uint32_t {
-      const __half hi = __float2half_rn(b);
-      const __half lo = __float2half_rn(b - __half2float(hi));
-      return (uint32_t)__half_as_ushort(hi) | ((uint32_t)__half_as_ushort(lo) << 16);
-    };
-    for (int n = tid; n < 64; n += 256) {             // W1^T: n < 64, k 0..7; bias in k 8, 9
-      *reinterpret_cast<uint4*>(s.b1 + tc::off(n, 0, 16)) = __ldg(img + (nn::I_W1T + n * 24) / 8);
-      *reinterpret_cast<uint4*>(s.b1 + tc::off(n, 8, 16)) = make_uint4(split(__ldg(nd.bias + n)), 0, 0, 0);
-      *reinterpret_cast<uint4*>(s.b2x + tc::off(n, 0, 16)) = make_uint4(split(__ldg(nd.bias + 64 + n)), 0, 0, 0);
-      *reinterpret_cast<uint4*>(s.b2x + tc::off(n, 8, 16)) = make_uint4(0, 0, 0, 0);
-    }
-    for (int n = tid; n < 16; n += 256) {
-      const uint32_t b = n < 7 ? split(__ldg(nd.bias + 128 + n)) : 0u;
-      *reinterpret_cast<uint4*>(s.b3x + tc::off(n, 0, 16)) = make_uint4(b, 0, 0, 0);
-      *reinterpret_cast<uint4*>(s.b3x + tc::off(n, 8, 16)) = make_uint4(0, 0, 0, 0);
-    }
-    for (int r = tid; r < 8; r += 256) {
-      *reinterpret_cast<uint4*>(s.ones + tc::off(r, 0, 16)) = make_uint4(0x3C003C00u, 0, 0, 0);
-      *reinterpret_cast<uint4*>(s.ones + tc::off(r, 8, 16)) = make_uint4(0, 0, 0, 0);
-    }
-    for (int e = tid; e < 64 * 8; e += 256) {        // W2^T: n < 64, k chunks of 8 (< 64)
-      const int n = e >> 3, kc = e & 7;
-      *reinterpret_cast<uint4*>(s.b2 + tc::off(n, 8 * kc, 64)) = __ldg(img + (nn::I_W2T + n * 72 + 8 * kc) / 8);
-    }
-    for (int e = tid; e < 16 * 8; e += 256) {        // W3^T: n < 16 (rows >= 8 zero)
-      const int n = e >> 3, kc = e & 7;
-      *reinterpret_cast<uint4*>(s.b3 + tc::off(n, 8 * kc, 64)) =
-          n < 8 ? __ldg(img + (nn::I_W3T + n * 72 + 8 * kc) / 8) : make_uint4(0, 0, 0, 0);
-    }
+    tc::stage_fwd_weights(nd, s.b1, s.b2, s.b3, s.b2x, s.b3x, s.ones, tid, 256);
     // columns 8..15 of A1: the ones that multiply W1's bias rows, then zeros (the
     // gathers write columns 0..7 only)
     *reinterpret_cast<uint4*>(G.a1 + tc::off(row, 8, 16)) = make_uint4(0x3C003C00u, 0, 0, 0);
@@ -560,90 +451,201 @@ __global__ void __launch_bounds__(256, 4) k_neural_stochastic_tc(NeuralDev nd, L
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(s.tmem), "n"(tc::TMEM_COLS));
 }
 
-// Deterministic: every tap of the filter window (at one level, or two blended by
-// frac(lod)) is decoded and the decoded values are weighted and summed.
+// Deterministic decode on the tensor cores: every tap of the filter window (at one
+// level, or at two blended by frac(lod)) is a row of a 128-row tile; a query takes R =
+// parts x T^2 consecutive rows (parts = 2 when the level is blended, else 1), so a tile
+// holds 128 / R queries.  Each thread gathers its tap's latent texel into the A tile
+// (zeros for fallback levels and for taps of queries without a texture value), the
+// three layers run as in the stochastic decode, and each row's output times its
+// weight (the tap weights wx wy times the level weight) is staged in shared memory;
+// the query's first row then sums its R rows.  Fallback levels use the stored texel.
+namespace tcd {
+
+struct Smem {
+  unsigned char b1[tc::B1_BYTES];
+  unsigned char b2[tc::B2_BYTES];
+  unsigned char b3[tc::B3_BYTES];
+  unsigned char b2x[64 * 16 * 2];
+  unsigned char b3x[16 * 16 * 2];
+  unsigned char ones[8 * 16 * 2];
+  unsigned char a1[tc::A1_BYTES];
+  unsigned char a2[tc::A2_BYTES];      // H1, then H2, then the weighted output rows
+  uint64_t bar;
+  uint32_t tmem;
+  int abort;
+};
+
+constexpr int TMEM_COLS = 64;
+
+}  // namespace tcd
+
+// One row of a deterministic tile: its query, weight and texel kind.  The texel (latent
+// or stored fallback) is gathered into the row of the A tile by cp.async.
+struct DetRow {
+  int64_t i;     // query
+  float w;       // tap weight times level weight (0: the row adds nothing)
+  int mode;      // 0: nothing, 1: decode the latent, 2: stored fallback texel
+};
+
 template <int F>
-__global__ void __launch_bounds__(128) k_neural_deterministic(NeuralDev nd, LookupArgs a) {
+__device__ __forceinline__ DetRow det_row(const NeuralDev& nd, const LookupArgs& a, int64_t i, int p, int tx,
+                                          int ty, uint4* arow) {
   using Fl = Filter<F>;
-  __shared__ __align__(16) NeuralSmem s;
-  stage_weights(nd, s.w, s.b, nn::IMG_FWD / 2);
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  uint32_t a2[2][4][4], a3[2][4][4];
-  const int64_t nwarps = (int64_t)gridDim.x * 4;
-  for (int64_t c = (int64_t)blockIdx.x * 4 + warp; c * 32 < a.n; c += nwarps) {
-    const int64_t i = c * 32 + lane;
-    const bool live = i < a.n;
-    float acc[7] = {0, 0, 0, 0, 0, 0, 0};
-    int lv[2] = {0, 0};
-    float lw[2] = {0.0f, 0.0f};
-    float2 uv = make_float2(0.f, 0.f);
-    if (live) {
-      uv = reinterpret_cast<const float2*>(a.coords)[i];
-      const float lod = a.lod ? a.lod[i] : 0.0f;
-      if (isfinite(lod) && isfinite(uv.x) && isfinite(uv.y)) {
-        lw[0] = 1.0f;
-        if (a.lod != nullptr && nd.nlev > 1) {
-          const float lc = fminf(fmaxf(lod, 0.0f), (float)(nd.nlev - 1));
-          if (a.level_mode == STF_LEVEL_NEAREST) {
-            lv[0] = min((int)floorf(__fadd_rn(lc, 0.5f)), nd.nlev - 1);
-          } else {
-            const float fl = floorf(lc), fr = __fsub_rn(lc, fl);
-            lv[0] = (int)fl;
-            lv[1] = min(lv[0] + 1, nd.nlev - 1);
-            lw[0] = 1.0f - fr;
-            lw[1] = fr;
-          }
-        }
-      }
-    }
-#pragma unroll 1
-    for (int p = 0; p < 2; ++p) {
-      if (!__any_sync(0xffffffffu, lw[p] > 0.0f)) continue;
-      const int L = lv[p];
-      float x[2] = {__fsub_rn(__fmul_rn(uv.x, (float)nd.lvl_w[L]), 0.5f),
-                    __fsub_rn(__fmul_rn(uv.y, (float)nd.lvl_h[L]), 0.5f)};
-      const bool ok = lw[p] > 0.0f && prepare_coords<2>(x);
-      float fx = 0.f, fy = 0.f;
-      int bx = 0, by = 0;
-      if (ok) {
-        bx = axis_base(x[0], fx) + Fl::OFF0;
-        by = axis_base(x[1], fy) + Fl::OFF0;
-      }
-      float wx[Fl::T], wy[Fl::T];
-      Fl::weights(fx, wx);
-      Fl::weights(fy, wy);
-#pragma unroll 1
-      for (int ty = 0; ty < Fl::T; ++ty) {
-#pragma unroll 1
-        for (int tx = 0; tx < Fl::T; ++tx) {
-          const float w = ok ? wx[tx] * wy[ty] * lw[p] : 0.0f;
-          uint4 texel = make_uint4(0, 0, 0, 0);
-          if (ok) texel = neural_texel(nd, L, bx + tx, by + ty);
-          const bool decode = ok && L < nd.nlat;
-          reinterpret_cast<uint4*>(s.a[warp])[lane] = decode ? texel : make_uint4(0, 0, 0, 0);
-          __syncwarp();
-          mlp_forward<2>(s.w, s.b, s.a[warp], 0, s.y[warp], a2, a3);
-          __syncwarp();
-          if (decode) {
-#pragma unroll
-            for (int k = 0; k < 7; ++k) acc[k] = fmaf(w, s.y[warp][lane][k], acc[k]);
-          } else if (ok) {
-            const uint32_t* tw = reinterpret_cast<const uint32_t*>(&texel);
-#pragma unroll
-            for (int k = 0; k < 7; ++k) {
-              const float2 f = unpack_h2(tw[k >> 1]);
-              acc[k] = fmaf(w, (k & 1) ? f.y : f.x, acc[k]);
-            }
-          }
-          __syncwarp();
-        }
-      }
-    }
-    if (live) {
-#pragma unroll
-      for (int k = 0; k < 7; ++k) a.out[i * 7 + k] = acc[k];
+  DetRow d;
+  d.i = i;
+  d.w = 0.0f;
+  d.mode = 0;
+  if (i >= a.n) return d;
+  const float2 uv = reinterpret_cast<const float2*>(a.coords)[i];
+  const float lod = a.lod ? a.lod[i] : 0.0f;
+  if (!(isfinite(lod) && isfinite(uv.x) && isfinite(uv.y))) return d;
+  float lw = p == 0 ? 1.0f : 0.0f;
+  int L = 0;
+  if (a.lod != nullptr && nd.nlev > 1) {
+    const float lc = fminf(fmaxf(lod, 0.0f), (float)(nd.nlev - 1));
+    if (a.level_mode == STF_LEVEL_NEAREST) {
+      L = min((int)floorf(__fadd_rn(lc, 0.5f)), nd.nlev - 1);
+    } else {
+      const float fl = floorf(lc), fr = __fsub_rn(lc, fl);
+      L = p == 0 ? (int)fl : min((int)fl + 1, nd.nlev - 1);
+      lw = p == 0 ? 1.0f - fr : fr;
     }
   }
+  const int w = nd.lvl_w[L], h = nd.lvl_h[L];
+  float x[2] = {__fsub_rn(__fmul_rn(uv.x, (float)w), 0.5f), __fsub_rn(__fmul_rn(uv.y, (float)h), 0.5f)};
+  if (!(lw > 0.0f) || !prepare_coords<2>(x)) return d;
+  float fx, fy;
+  const int bx = axis_base(x[0], fx) + Fl::OFF0, by = axis_base(x[1], fy) + Fl::OFF0;
+  float wx[Fl::T], wy[Fl::T];
+  Fl::weights(fx, wx);
+  Fl::weights(fy, wy);
+  float wxs = wx[0], wys = wy[0];
+#pragma unroll
+  for (int k = 1; k < Fl::T; ++k) {
+    if (tx == k) wxs = wx[k];
+    if (ty == k) wys = wy[k];
+  }
+  d.w = wxs * wys * lw;
+  const int cx = min(max(bx + tx, 0), w - 1), cy = min(max(by + ty, 0), h - 1);
+  const __half* base = L < nd.nlat ? nd.lat16 : nd.fb16;
+  cp_async16(arow, base + (nd.lvl_off[L] + (int64_t)cy * w + cx) * 8);
+  d.mode = L < nd.nlat ? 1 : 2;
+  return d;
+}
+
+template <int F>
+__global__ void __launch_bounds__(128, 6) k_neural_deterministic_tc(NeuralDev nd, LookupArgs a) {
+  using Fl = Filter<F>;
+  extern __shared__ __align__(1024) unsigned char dyn[];
+  tcd::Smem& s = *reinterpret_cast<tcd::Smem*>(dyn);
+  const int tid = threadIdx.x, warp = tid >> 5;
+  tc::stage_fwd_weights(nd, s.b1, s.b2, s.b3, s.b2x, s.b3x, s.ones, tid, 128);
+  uint4* arow = reinterpret_cast<uint4*>(s.a1 + tc::off(tid, 0, 16));
+  *reinterpret_cast<uint4*>(s.a1 + tc::off(tid, 8, 16)) = make_uint4(0x3C003C00u, 0, 0, 0);
+  if (tid == 0) {
+    s.abort = 0;
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"((uint32_t)__cvta_generic_to_shared(&s.bar)));
+    asm volatile("fence.mbarrier_init.release.cluster;");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     (uint32_t)__cvta_generic_to_shared(&s.tmem)), "n"(tcd::TMEM_COLS));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  const uint32_t tmem = s.tmem;
+  const uint32_t trow = tmem + ((uint32_t)(32 * warp) << 16);
+  uint32_t parity = 0;
+  auto run = [&](auto issue) -> bool {
+    asm volatile("fence.proxy.async.shared::cta;");
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    if (tid == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;");
+      issue();
+      tc::commit(&s.bar);
+      if (!tc::wait_bar(&s.bar, parity)) s.abort = 1;
+    }
+    parity ^= 1;
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    return s.abort == 0;
+  };
+  constexpr int T2 = Fl::T * Fl::T;
+  const int parts = (a.lod != nullptr && nd.nlev > 1 && a.level_mode != STF_LEVEL_NEAREST) ? 2 : 1;
+  const int R = parts * T2;                    // rows per query: 4, 8, 16 or 32
+  const int Q = 128 / R;                       // queries per tile
+  const int qi = tid / R, sub = tid % R, p = sub / T2, tap = sub % T2;
+  const int tx = tap % Fl::T, ty = tap / Fl::T;
+  float* stage = reinterpret_cast<float*>(s.a2);
+  const int64_t ntiles = (a.n + Q - 1) / Q;
+  int64_t tile = blockIdx.x;
+  DetRow cur;
+  if (tile < ntiles) cur = det_row<F>(nd, a, tile * Q + qi, p, tx, ty, arow);
+  cp_async_commit();
+  for (; tile < ntiles; tile += gridDim.x) {
+    cp_async_wait<0>();
+    uint4 fb = make_uint4(0, 0, 0, 0);
+    if (cur.mode == 2) fb = *arow;               // stored fallback texel (own row)
+    if (cur.mode != 1) *arow = make_uint4(0, 0, 0, 0);
+    if (!run([&] { tc::mma(tmem, tc::desc(s.a1, 16), tc::desc(s.b1, 16), tc::idesc(128, 64), 0); })) break;
+    // A1 is free: gather the next tile's texels while this tile's layers run
+    const int64_t next = tile + gridDim.x;
+    DetRow nxt;
+    if (next < ntiles) nxt = det_row<F>(nd, a, next * Q + qi, p, tx, ty, arow);
+    cp_async_commit();
+    tc_hidden(trow, s.a2, tid);
+    if (!run([&] {
+          for (int kk = 0; kk < 4; ++kk)
+            tc::mma(tmem, tc::desc(s.a2 + kk * 256, 64), tc::desc(s.b2 + kk * 256, 64), tc::idesc(128, 64), kk);
+          tc::mma(tmem, tc::desc_rows_repeated(s.ones), tc::desc(s.b2x, 16), tc::idesc(128, 64), 1);
+        }))
+      break;
+    tc_hidden(trow, s.a2, tid);
+    if (!run([&] {
+          for (int kk = 0; kk < 4; ++kk)
+            tc::mma(tmem, tc::desc(s.a2 + kk * 256, 64), tc::desc(s.b3 + kk * 256, 64), tc::idesc(128, 16), kk);
+          tc::mma(tmem, tc::desc_rows_repeated(s.ones), tc::desc(s.b3x, 16), tc::idesc(128, 16), 1);
+        }))
+      break;
+    float v[8];
+    {
+      uint32_t r[8];
+      tc::tmem_ld<8>(trow, r);
+#pragma unroll
+      for (int k = 0; k < 7; ++k) v[k] = __uint_as_float(r[k]);
+    }
+    if (cur.mode == 2) {
+      const uint32_t* tw = reinterpret_cast<const uint32_t*>(&fb);
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const float2 f = unpack_h2(tw[k]);
+        v[2 * k] = f.x;
+        v[2 * k + 1] = f.y;
+      }
+    }
+    // A2 (H2) has been consumed by layer 3: it now stages the weighted rows
+#pragma unroll
+    for (int k = 0; k < 7; ++k) stage[tid * 8 + k] = cur.mode ? cur.w * v[k] : 0.0f;
+    __syncthreads();
+    if (sub == 0 && cur.i < a.n) {
+      float acc[7] = {0, 0, 0, 0, 0, 0, 0};
+      for (int rr = 0; rr < R; ++rr)
+#pragma unroll
+        for (int k = 0; k < 7; ++k) acc[k] += stage[(tid + rr) * 8 + k];
+#pragma unroll
+      for (int k = 0; k < 7; ++k) a.out[cur.i * 7 + k] = acc[k];
+    }
+    cur = nxt;
+    // the next tile's first barrier orders these reads before A2 is rewritten
+  }
+  cp_async_wait<0>();
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  if (tid == 0 && s.abort) atomicOr(nd.status, STF_DEV_MMA_TIMEOUT);
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(s.tmem), "n"(tcd::TMEM_COLS));
 }
 
 // ---------------------------------------------------------------- training
@@ -703,28 +705,156 @@ __device__ __forceinline__ int64_t permute_index(int64_t x, int64_t n, uint64_t 
   return x % n;   // unreachable in practice: cycles return to [0, n) within a few steps
 }
 
-struct TrainSmem {
-  uint32_t w[nn::IMG_ALL / 2];
-  float b[nn::NBIAS];
-  uint32_t a[4][32 * 4];    // latent rows (binary16)
-  uint32_t d[4][32 * 4];    // dY rows (binary16)
-  float y[4][32][8];        // Y rows, then dX rows
+// ---------------------------------------------------------------- tcgen05 training
+//
+// Forward and backward of the decoder for tiles of 128 training texels on the
+// fifth-generation tensor cores: six tcgen05.mma round trips per tile (M = 128,
+// binary16 operands in shared memory, float32 accumulators in tensor memory), issued
+// by one thread, each followed by an epilogue in which every thread reads its row:
+//   H1 = ReLU(X W1 + b1), H2 = ReLU(H1 W2 + b2), Y = H2 W3 + b3       (forward)
+//   dY = 2 (Y - T) / B, dA2 = (dY W3^T) [H2 > 0], dA1 = (dA2 W2^T) [H1 > 0],
+//   dX = dA1 W1^T                                                      (backward)
+// The biases enter the forward MMAs as an extra K chunk against columns of ones, as in
+// the decode.  The activations of the batch go to global memory for the weight
+// gradients; the latents take an Adam step (training) or their gradients are returned.
+
+namespace tct {
+
+struct Smem {
+  unsigned char b1[tc::B1_BYTES];      // W1^T (64 x 16): k 0..7, biases (hi, lo) in k 8, 9
+  unsigned char b2[tc::B2_BYTES];      // W2^T (64 x 64)
+  unsigned char b3[tc::B3_BYTES];      // W3^T (16 x 64), rows >= 7 zero
+  unsigned char b2x[64 * 16 * 2];      // (b2_hi, b2_lo) in k 0, 1
+  unsigned char b3x[16 * 16 * 2];      // (b3_hi, b3_lo) in k 0, 1
+  unsigned char ones[8 * 16 * 2];      // one 8-row group: 1 in columns 0, 1
+  unsigned char r3[64 * 16 * 2];       // W3 (64 x 16): B of dY W3^T (k = output, < 7)
+  unsigned char r2[64 * 64 * 2];       // W2 (64 x 64): B of dA2 W2^T
+  unsigned char r1[16 * 64 * 2];       // W1 (16 x 64), rows >= 8 zero: B of dA1 W1^T
+  unsigned char x[128 * 16 * 2];       // latents in k 0..7, ones in k 8, 9
+  unsigned char h1[128 * 64 * 2];
+  unsigned char h2[128 * 64 * 2];
+  unsigned char dy[128 * 16 * 2];      // dY in k 0..6, zeros beyond
+  unsigned char da2[128 * 64 * 2];
+  unsigned char da1[128 * 64 * 2];
+  uint64_t bar;
+  uint32_t tmem;
+  int abort;
 };
 
-// Forward and backward of 32 texels per warp iteration: stores the batch's
-// activations for the weight gradients, accumulates the loss and either applies
-// Adam to the latents (training) or returns their gradients.
-__global__ void __launch_bounds__(128) k_neural_fwd_bwd(NeuralDev nd, TrainArgs ta, ActBuffers act) {
-  __shared__ __align__(16) TrainSmem s;
-  stage_weights(nd, s.w, s.b, nn::IMG_ALL / 2);
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
-  const uint32_t* w3r = s.w + nn::I_W3R / 2;
-  const uint32_t* w2r = s.w + nn::I_W2R / 2;
-  const uint32_t* w1r = s.w + nn::I_W1R / 2;
+constexpr int TMEM_COLS = 64;
+
+}  // namespace tct
+
+// Forward hidden epilogue with the row also written to global memory (the batch's
+// activations for the weight gradients): D -> ReLU -> binary16 -> A tile row, grow.
+__device__ __forceinline__ void tc_hidden_keep(uint32_t taddr, unsigned char* tile, int row, uint4* grow) {
+#pragma unroll
+  for (int half = 0; half < 2; ++half) {
+    uint32_t r[32];
+    tc::tmem_ld<32>(taddr + 32 * half, r);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      uint32_t w[4];
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const int c = 8 * q + 2 * e;
+        asm("cvt.rn.relu.f16x2.f32 %0, %1, %2;" : "=r"(w[e]) : "f"(__uint_as_float(r[c + 1])), "f"(__uint_as_float(r[c])));
+      }
+      const uint4 v = make_uint4(w[0], w[1], w[2], w[3]);
+      *reinterpret_cast<uint4*>(tile + tc::off(row, 32 * half + 8 * q, 64)) = v;
+      if (grow) grow[4 * half + q] = v;
+    }
+  }
+}
+
+// Backward epilogue: D (64 float32) masked by the row of the forward activation tile
+// (kept where the activation is > 0, the ReLU derivative) -> binary16 -> A tile row,
+// and to global memory.
+__device__ __forceinline__ void tc_masked_keep(uint32_t taddr, const unsigned char* mask, unsigned char* tile,
+                                               int row, uint4* grow) {
+#pragma unroll
+  for (int half = 0; half < 2; ++half) {
+    uint32_t r[32];
+    tc::tmem_ld<32>(taddr + 32 * half, r);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const uint4 m = *reinterpret_cast<const uint4*>(mask + tc::off(row, 32 * half + 8 * q, 64));
+      const uint32_t mw[4] = {m.x, m.y, m.z, m.w};
+      uint32_t w[4];
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const int c = 8 * q + 2 * e;
+        const float2 h = unpack_h2(mw[e]);
+        w[e] = pack_h2(h.x > 0.f ? __uint_as_float(r[c]) : 0.f, h.y > 0.f ? __uint_as_float(r[c + 1]) : 0.f);
+      }
+      const uint4 v = make_uint4(w[0], w[1], w[2], w[3]);
+      *reinterpret_cast<uint4*>(tile + tc::off(row, 32 * half + 8 * q, 64)) = v;
+      if (grow) grow[4 * half + q] = v;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(128, 2) k_neural_fwd_bwd_tc(NeuralDev nd, TrainArgs ta, ActBuffers act) {
+  extern __shared__ __align__(1024) unsigned char dyn[];
+  tct::Smem& s = *reinterpret_cast<tct::Smem*>(dyn);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  {
+    const uint4* img = reinterpret_cast<const uint4*>(nd.wimg);
+    const uint4 z = make_uint4(0, 0, 0, 0);
+    tc::stage_fwd_weights(nd, s.b1, s.b2, s.b3, s.b2x, s.b3x, s.ones, tid, 128);
+    for (int n = tid; n < 64; n += 128) {      // W3 rows (k = output) for dY W3^T
+      *reinterpret_cast<uint4*>(s.r3 + tc::off(n, 0, 16)) = __ldg(img + (nn::I_W3R + n * 8) / 8);
+      *reinterpret_cast<uint4*>(s.r3 + tc::off(n, 8, 16)) = z;
+    }
+    for (int e = tid; e < 64 * 8; e += 128) {  // W2 rows for dA2 W2^T
+      const int n = e >> 3, kc = e & 7;
+      *reinterpret_cast<uint4*>(s.r2 + tc::off(n, 8 * kc, 64)) = __ldg(img + (nn::I_W2R + n * 72 + 8 * kc) / 8);
+    }
+    for (int e = tid; e < 16 * 8; e += 128) {  // W1 rows (rows >= 8 zero) for dA1 W1^T
+      const int n = e >> 3, kc = e & 7;
+      *reinterpret_cast<uint4*>(s.r1 + tc::off(n, 8 * kc, 64)) =
+          n < 8 ? __ldg(img + (nn::I_W1R + n * 72 + 8 * kc) / 8) : z;
+    }
+    *reinterpret_cast<uint4*>(s.x + tc::off(tid, 8, 16)) = make_uint4(0x3C003C00u, 0, 0, 0);
+    *reinterpret_cast<uint4*>(s.dy + tc::off(tid, 8, 16)) = z;
+  }
+  if (tid == 0) {
+    s.abort = 0;
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"((uint32_t)__cvta_generic_to_shared(&s.bar)));
+    asm volatile("fence.mbarrier_init.release.cluster;");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     (uint32_t)__cvta_generic_to_shared(&s.tmem)), "n"(tct::TMEM_COLS));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  const uint32_t tmem = s.tmem;
+  const uint32_t trow = tmem + ((uint32_t)(32 * warp) << 16);   // this warp's lanes
+  uint32_t parity = 0;
+  // make the tiles written so far visible to the tensor cores, let one thread issue
+  // the MMAs, wait for them (bounded), and release every thread to read the result
+  auto run = [&](auto issue) -> bool {
+    asm volatile("fence.proxy.async.shared::cta;");
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    if (tid == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;");
+      issue();
+      tc::commit(&s.bar);
+      if (!tc::wait_bar(&s.bar, parity)) s.abort = 1;
+    }
+    parity ^= 1;
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    return s.abort == 0;
+  };
   float loss_part = 0.0f;
-  const int64_t nwarps = (int64_t)gridDim.x * 4;
-  for (int64_t c = (int64_t)blockIdx.x * 4 + warp; c * 32 < ta.batch; c += nwarps) {
-    const int64_t r = c * 32 + lane;
+  const int64_t ntiles = (ta.batch + 127) / 128;
+  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int64_t r = tile * 128 + tid;
     const bool live = r < ta.batch;
     int64_t id = 0, epoch = 0;
     float T[7] = {0, 0, 0, 0, 0, 0, 0};
@@ -747,95 +877,62 @@ __global__ void __launch_bounds__(128) k_neural_fwd_bwd(NeuralDev nd, TrainArgs 
     }
     const uint4 xh = make_uint4(pack_h2(X[0], X[1]), pack_h2(X[2], X[3]), pack_h2(X[4], X[5]),
                                 pack_h2(X[6], X[7]));
-    reinterpret_cast<uint4*>(s.a[warp])[lane] = xh;
+    *reinterpret_cast<uint4*>(s.x + tc::off(tid, 0, 16)) = xh;
     if (live) reinterpret_cast<uint4*>(act.x)[r] = xh;
-    __syncwarp();
-#pragma unroll 1
-    for (int m = 0; m < 2; ++m) {
-      uint32_t a2[1][4][4], a3[1][4][4];
-      mlp_forward<1>(s.w, s.b, s.a[warp], 16 * m, s.y[warp], a2, a3);
-      const int64_t rg = c * 32 + 16 * m + g, rh = rg + 8;   // batch rows of this lane's fragments
-      const bool lg = rg < ta.batch, lh = rh < ta.batch;
+    // forward
+    if (!run([&] { tc::mma(tmem, tc::desc(s.x, 16), tc::desc(s.b1, 16), tc::idesc(128, 64), 0); })) break;
+    tc_hidden_keep(trow, s.h1, tid, live ? reinterpret_cast<uint4*>(act.h1) + r * 8 : nullptr);
+    if (!run([&] {
+          for (int kk = 0; kk < 4; ++kk)
+            tc::mma(tmem, tc::desc(s.h1 + kk * 256, 64), tc::desc(s.b2 + kk * 256, 64), tc::idesc(128, 64), kk);
+          tc::mma(tmem, tc::desc_rows_repeated(s.ones), tc::desc(s.b2x, 16), tc::idesc(128, 64), 1);
+        }))
+      break;
+    tc_hidden_keep(trow, s.h2, tid, live ? reinterpret_cast<uint4*>(act.h2) + r * 8 : nullptr);
+    if (!run([&] {
+          for (int kk = 0; kk < 4; ++kk)
+            tc::mma(tmem, tc::desc(s.h2 + kk * 256, 64), tc::desc(s.b3 + kk * 256, 64), tc::idesc(128, 16), kk);
+          tc::mma(tmem, tc::desc_rows_repeated(s.ones), tc::desc(s.b3x, 16), tc::idesc(128, 16), 1);
+        }))
+      break;
+    {
+      uint32_t y[8];
+      tc::tmem_ld<8>(trow, y);
+      float d[8];
 #pragma unroll
-      for (int kc = 0; kc < 4; ++kc) {
-#pragma unroll
-        for (int q = 0; q < 2; ++q) {
-          const int col2 = 8 * kc + 4 * q + t;   // 32-bit word column of hidden pair
-          if (lg) reinterpret_cast<uint32_t*>(act.h1)[rg * 32 + col2] = a2[0][kc][2 * q];
-          if (lh) reinterpret_cast<uint32_t*>(act.h1)[rh * 32 + col2] = a2[0][kc][2 * q + 1];
-          if (lg) reinterpret_cast<uint32_t*>(act.h2)[rg * 32 + col2] = a3[0][kc][2 * q];
-          if (lh) reinterpret_cast<uint32_t*>(act.h2)[rh * 32 + col2] = a3[0][kc][2 * q + 1];
-        }
+      for (int k = 0; k < 7; ++k) {
+        const float e = live ? __uint_as_float(y[k]) - T[k] : 0.0f;
+        loss_part = fmaf(e, e, loss_part);
+        d[k] = 2.0f * ta.inv_batch * e;
       }
-      __syncwarp();
-      // dY = 2 (Y - T) / B for the rows of this tile (lanes 16m .. 16m + 15)
-      if ((lane >> 4) == m) {
-        float d[8];
+      d[7] = 0.0f;
+      const uint4 dh = make_uint4(pack_h2(d[0], d[1]), pack_h2(d[2], d[3]), pack_h2(d[4], d[5]),
+                                  pack_h2(d[6], d[7]));
+      *reinterpret_cast<uint4*>(s.dy + tc::off(tid, 0, 16)) = dh;
+      if (live) reinterpret_cast<uint4*>(act.dy)[r] = dh;
+    }
+    // backward
+    if (!run([&] { tc::mma(tmem, tc::desc(s.dy, 16), tc::desc(s.r3, 16), tc::idesc(128, 64), 0); })) break;
+    tc_masked_keep(trow, s.h2, s.da2, tid, live ? reinterpret_cast<uint4*>(act.da2) + r * 8 : nullptr);
+    if (!run([&] {
+          for (int kk = 0; kk < 4; ++kk)
+            tc::mma(tmem, tc::desc(s.da2 + kk * 256, 64), tc::desc(s.r2 + kk * 256, 64), tc::idesc(128, 64), kk);
+        }))
+      break;
+    tc_masked_keep(trow, s.h1, s.da1, tid, live ? reinterpret_cast<uint4*>(act.da1) + r * 8 : nullptr);
+    if (!run([&] {
+          for (int kk = 0; kk < 4; ++kk)
+            tc::mma(tmem, tc::desc(s.da1 + kk * 256, 64), tc::desc(s.r1 + kk * 256, 64), tc::idesc(128, 16), kk);
+        }))
+      break;
+    float dx[8];
+    {
+      uint32_t q[8];
+      tc::tmem_ld<8>(trow, q);
 #pragma unroll
-        for (int k = 0; k < 7; ++k) {
-          const float e = live ? s.y[warp][lane][k] - T[k] : 0.0f;
-          loss_part = fmaf(e, e, loss_part);
-          d[k] = 2.0f * ta.inv_batch * e;
-        }
-        d[7] = 0.0f;
-        const uint4 dh = make_uint4(pack_h2(d[0], d[1]), pack_h2(d[2], d[3]), pack_h2(d[4], d[5]),
-                                    pack_h2(d[6], d[7]));
-        reinterpret_cast<uint4*>(s.d[warp])[lane] = dh;
-        if (live) reinterpret_cast<uint4*>(act.dy)[r] = dh;
-      }
-      __syncwarp();
-      uint32_t ady[4] = {s.d[warp][(16 * m + g) * 4 + t], s.d[warp][(16 * m + g + 8) * 4 + t], 0u, 0u};
-      // dA2 = (dY W3^T) * [H2 > 0]
-      uint32_t da2[4][4];
-#pragma unroll
-      for (int j = 0; j < 8; ++j) {
-        float cc[4] = {0.f, 0.f, 0.f, 0.f};
-        mma16816(cc, ady, w3r[(8 * j + g) * nn::S8 + t], 0u);
-        const float2 hl = unpack_h2(a3[0][j >> 1][(j & 1) * 2]);
-        const float2 hh = unpack_h2(a3[0][j >> 1][(j & 1) * 2 + 1]);
-        const uint32_t lo = pack_h2(hl.x > 0.f ? cc[0] : 0.f, hl.y > 0.f ? cc[1] : 0.f);
-        const uint32_t hi = pack_h2(hh.x > 0.f ? cc[2] : 0.f, hh.y > 0.f ? cc[3] : 0.f);
-        da2[j >> 1][(j & 1) * 2] = lo;
-        da2[j >> 1][(j & 1) * 2 + 1] = hi;
-        const int col2 = 4 * j + t;
-        if (lg) reinterpret_cast<uint32_t*>(act.da2)[rg * 32 + col2] = lo;
-        if (lh) reinterpret_cast<uint32_t*>(act.da2)[rh * 32 + col2] = hi;
-      }
-      // dA1 = (dA2 W2^T) * [H1 > 0]
-      uint32_t da1[4][4];
-#pragma unroll
-      for (int j = 0; j < 8; ++j) {
-        float cc[4] = {0.f, 0.f, 0.f, 0.f};
-#pragma unroll
-        for (int kc = 0; kc < 4; ++kc)
-          mma16816(cc, da2[kc], w2r[(8 * j + g) * nn::S72 + 8 * kc + t],
-                   w2r[(8 * j + g) * nn::S72 + 8 * kc + 4 + t]);
-        const float2 hl = unpack_h2(a2[0][j >> 1][(j & 1) * 2]);
-        const float2 hh = unpack_h2(a2[0][j >> 1][(j & 1) * 2 + 1]);
-        const uint32_t lo = pack_h2(hl.x > 0.f ? cc[0] : 0.f, hl.y > 0.f ? cc[1] : 0.f);
-        const uint32_t hi = pack_h2(hh.x > 0.f ? cc[2] : 0.f, hh.y > 0.f ? cc[3] : 0.f);
-        da1[j >> 1][(j & 1) * 2] = lo;
-        da1[j >> 1][(j & 1) * 2 + 1] = hi;
-        const int col2 = 4 * j + t;
-        if (lg) reinterpret_cast<uint32_t*>(act.da1)[rg * 32 + col2] = lo;
-        if (lh) reinterpret_cast<uint32_t*>(act.da1)[rh * 32 + col2] = hi;
-      }
-      // dX = dA1 W1^T
-      float cx[4] = {0.f, 0.f, 0.f, 0.f};
-#pragma unroll
-      for (int kc = 0; kc < 4; ++kc)
-        mma16816(cx, da1[kc], w1r[g * nn::S72 + 8 * kc + t], w1r[g * nn::S72 + 8 * kc + 4 + t]);
-      __syncwarp();
-      s.y[warp][16 * m + g][2 * t] = cx[0];
-      s.y[warp][16 * m + g][2 * t + 1] = cx[1];
-      s.y[warp][16 * m + g + 8][2 * t] = cx[2];
-      s.y[warp][16 * m + g + 8][2 * t + 1] = cx[3];
-      __syncwarp();
+      for (int k = 0; k < 8; ++k) dx[k] = __uint_as_float(q[k]);
     }
     if (live) {
-      float dx[8];
-#pragma unroll
-      for (int k = 0; k < 8; ++k) dx[k] = s.y[warp][lane][k];
       if (ta.dx_out) {
 #pragma unroll
         for (int k = 0; k < 8; ++k) ta.dx_out[r * 8 + k] = dx[k];
@@ -860,126 +957,196 @@ __global__ void __launch_bounds__(128) k_neural_fwd_bwd(NeuralDev nd, TrainArgs 
                        pack_h2(xn[6], xn[7]));
       }
     }
-    __syncwarp();
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) loss_part += __shfl_xor_sync(0xffffffffu, loss_part, o);
   if (lane == 0) atomicAdd(ta.loss, loss_part * ta.inv_batch);
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  if (tid == 0 && s.abort) atomicOr(nd.status, STF_DEV_MMA_TIMEOUT);
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(s.tmem), "n"(tct::TMEM_COLS));
 }
 
-// Weight and bias gradients of one batch: dW1 = X^T dA1, dW2 = H1^T dA2, dW3 = H2^T dY,
-// db = column sums.  Each CTA reduces 64-row chunks; warp w owns rows 16w..16w+15 of
-// dW2 and dW3 and columns 16w..16w+15 of dW1.  Partial sums are added atomically.
-struct WgradSmem {
-  __half x[64][24];
-  __half h1[64][72];
-  __half h2[64][72];
-  __half dy[64][8];
-  __half da2[64][72];
-  __half da1[64][72];
+// Weight and bias gradients on the tensor cores.  The batch is the reduction (K)
+// dimension, so each chunk of 128 batch rows is staged transposed (feature-major, K
+// = batch row) into K-major operand tiles, and two accumulating tcgen05.mma chains per
+// chunk sum over the CTA's chunks in tensor memory:
+//   D1 (128 x 80)  = [H1^T; H2^T] [dA2^T; dY^T]^T : dW2 = rows 0..63 x cols 0..63,
+//                                                    dW3 = rows 64..127 x cols 64..70
+//   D2 (128 x 144) = [X^T; 1; 0] [dA1^T; dA2^T; dY^T]^T : dW1 = rows 0..7 x cols 0..63,
+//                                                    db1, db2, db3 = row 8
+// (the other blocks of the products are not used).  One CTA-wide atomic add per
+// gradient entry at the end.
+namespace tcw {
+
+struct Smem {
+  unsigned char a1[128 * 128 * 2];   // H1^T (rows 0..63), H2^T (rows 64..127)
+  unsigned char a2[128 * 128 * 2];   // X^T (rows 0..7), ones (row 8), zeros
+  unsigned char b[144 * 128 * 2];    // dA1^T (rows 0..63), dA2^T (64..127), dY^T (128..143)
+  uint64_t bar;
+  uint32_t tmem;
+  int abort;
 };
 
-__global__ void __launch_bounds__(128) k_neural_wgrad(ActBuffers act, int64_t batch, float* grads) {
-  __shared__ __align__(16) WgradSmem s;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
-  const int mi = lane >> 3, mr = lane & 7;   // ldmatrix: matrix index, row within it
-  float w2acc[8][4], w3acc[4], w1acc[2][4];
+constexpr int TMEM_COLS = 256;   // D1 in columns 0..79, D2 in 96..239
+
+}  // namespace tcw
+
+// Element (m, k) of a K-major operand tile with K = 128.
+__device__ __forceinline__ __half* t128(unsigned char* tile, int m, int k) {
+  return reinterpret_cast<__half*>(tile + tc::off(m, k, 128));
+}
+
+__device__ __forceinline__ void scatter_row(unsigned char* tile, int m0, int k, uint4 v) {
+  const __half* h = reinterpret_cast<const __half*>(&v);
 #pragma unroll
-  for (int j = 0; j < 8; ++j) w2acc[j][0] = w2acc[j][1] = w2acc[j][2] = w2acc[j][3] = 0.f;
-  w3acc[0] = w3acc[1] = w3acc[2] = w3acc[3] = 0.f;
-  w1acc[0][0] = w1acc[0][1] = w1acc[0][2] = w1acc[0][3] = 0.f;
-  w1acc[1][0] = w1acc[1][1] = w1acc[1][2] = w1acc[1][3] = 0.f;
-  float bsum[2] = {0.f, 0.f};   // bias columns threadIdx.x and threadIdx.x + 128 (< 136)
-  for (int64_t c0 = (int64_t)blockIdx.x * 64; c0 < batch; c0 += (int64_t)gridDim.x * 64) {
-    // stage 64 rows (zero beyond the batch), 16-byte copies
-    for (int k = threadIdx.x; k < 64 * 8; k += 128) {
-      const int row = k >> 3, q = k & 7;
-      const int64_t gr = c0 + row;
-      const bool in = gr < batch;
-      const uint4 z = make_uint4(0, 0, 0, 0);
-      reinterpret_cast<uint4*>(&s.h1[row][0])[q] = in ? reinterpret_cast<const uint4*>(act.h1 + gr * 64)[q] : z;
-      reinterpret_cast<uint4*>(&s.h2[row][0])[q] = in ? reinterpret_cast<const uint4*>(act.h2 + gr * 64)[q] : z;
-      reinterpret_cast<uint4*>(&s.da2[row][0])[q] = in ? reinterpret_cast<const uint4*>(act.da2 + gr * 64)[q] : z;
-      reinterpret_cast<uint4*>(&s.da1[row][0])[q] = in ? reinterpret_cast<const uint4*>(act.da1 + gr * 64)[q] : z;
-      if (q == 0) {
-        reinterpret_cast<uint4*>(&s.x[row][0])[0] = in ? reinterpret_cast<const uint4*>(act.x + gr * 8)[0] : z;
-        reinterpret_cast<uint4*>(&s.x[row][0])[1] = z;
-        reinterpret_cast<uint4*>(&s.dy[row][0])[0] = in ? reinterpret_cast<const uint4*>(act.dy + gr * 8)[0] : z;
-      }
-    }
-    __syncthreads();
-#pragma unroll 1
-    for (int kc = 0; kc < 4; ++kc) {
-      const int k0 = 16 * kc;
-      // A = H1^T tile (hidden 16w.., batch k0..): matrix mi covers rows k0 + 8*(mi/2), cols 16w + 8*(mi%2)
-      uint32_t ah1[4], ah2[4], ax[4];
-      ldsm_x4_trans(ah1, &s.h1[k0 + mr + 8 * (mi >> 1)][16 * warp + 8 * (mi & 1)]);
-      ldsm_x4_trans(ah2, &s.h2[k0 + mr + 8 * (mi >> 1)][16 * warp + 8 * (mi & 1)]);
-      ldsm_x4_trans(ax, &s.x[k0 + mr + 8 * (mi >> 1)][8 * (mi & 1)]);
-#pragma unroll
-      for (int p = 0; p < 4; ++p) {
-        // B = dA2 columns 16p .. 16p+15: matrices (k lo, n 16p), (k hi, n 16p), (k lo, n 16p+8), (k hi, n 16p+8)
-        uint32_t b[4];
-        ldsm_x4_trans(b, &s.da2[k0 + mr + 8 * (mi & 1)][16 * p + 8 * (mi >> 1)]);
-        mma16816(w2acc[2 * p], ah1, b[0], b[1]);
-        mma16816(w2acc[2 * p + 1], ah1, b[2], b[3]);
-      }
-      {
-        uint32_t b[2];
-        ldsm_x2_trans(b, &s.dy[k0 + mr + 8 * (mi & 1)][0]);
-        mma16816(w3acc, ah2, b[0], b[1]);
-      }
-      {
-        uint32_t b[4];
-        ldsm_x4_trans(b, &s.da1[k0 + mr + 8 * (mi & 1)][16 * warp + 8 * (mi >> 1)]);
-        mma16816(w1acc[0], ax, b[0], b[1]);
-        mma16816(w1acc[1], ax, b[2], b[3]);
-      }
-    }
-    for (int q = 0; q < 2; ++q) {
-      const int k = threadIdx.x + 128 * q;
-      if (k >= nn::NBIAS) break;
-      for (int row = 0; row < 64; ++row) {
-        if (k < 64) bsum[q] += __half2float(s.da1[row][k]);
-        else if (k < 128) bsum[q] += __half2float(s.da2[row][k - 64]);
-        else bsum[q] += __half2float(s.dy[row][k - 128]);
-      }
-    }
-    __syncthreads();
-  }
-  // dW2[m][n]: m = 16w + g (+8), n = 8j + 2t (+1)
-#pragma unroll
-  for (int j = 0; j < 8; ++j) {
-    const int n = 8 * j + 2 * t, m = 16 * warp + g;
-    atomicAdd(grads + nn::P_W2 + m * 64 + n, w2acc[j][0]);
-    atomicAdd(grads + nn::P_W2 + m * 64 + n + 1, w2acc[j][1]);
-    atomicAdd(grads + nn::P_W2 + (m + 8) * 64 + n, w2acc[j][2]);
-    atomicAdd(grads + nn::P_W2 + (m + 8) * 64 + n + 1, w2acc[j][3]);
-  }
+  for (int e = 0; e < 8; ++e) *t128(tile, m0 + e, k) = h[e];
+}
+
+__global__ void __launch_bounds__(128, 2) k_neural_wgrad_tc(ActBuffers act, int64_t batch, float* grads,
+                                                            unsigned* status) {
+  extern __shared__ __align__(1024) unsigned char dyn[];
+  tcw::Smem& s = *reinterpret_cast<tcw::Smem*>(dyn);
+  const int tid = threadIdx.x, warp = tid >> 5;
   {
-    const int o = 2 * t, m = 16 * warp + g;
-    if (o < 7) {
-      atomicAdd(grads + nn::P_W3 + m * 7 + o, w3acc[0]);
-      atomicAdd(grads + nn::P_W3 + (m + 8) * 7 + o, w3acc[2]);
-    }
-    if (o + 1 < 7) {
-      atomicAdd(grads + nn::P_W3 + m * 7 + o + 1, w3acc[1]);
-      atomicAdd(grads + nn::P_W3 + (m + 8) * 7 + o + 1, w3acc[3]);
-    }
+    const uint4 z = make_uint4(0, 0, 0, 0);
+    for (int e = tid; e < 128 * 128 * 2 / 16; e += 128) reinterpret_cast<uint4*>(s.a2)[e] = z;
   }
+  __syncthreads();
+  *t128(s.a2, 8, tid) = __float2half_rn(1.0f);
+  if (tid == 0) {
+    s.abort = 0;
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"((uint32_t)__cvta_generic_to_shared(&s.bar)));
+    asm volatile("fence.mbarrier_init.release.cluster;");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     (uint32_t)__cvta_generic_to_shared(&s.tmem)), "n"(tcw::TMEM_COLS));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  const uint32_t d1 = s.tmem, d2 = s.tmem + 96;
+  uint32_t parity = 0;
+  int chunks_done = 0;
+  const int64_t nchunks = (batch + 127) / 128;
+  for (int64_t c = blockIdx.x; c < nchunks; c += gridDim.x) {
+    // stage this thread's batch row (zeros beyond the batch) as column k = tid
+    const int64_t r = c * 128 + tid;
+    const bool live = r < batch;
+    const uint4 z = make_uint4(0, 0, 0, 0);
+    const uint4* h1 = reinterpret_cast<const uint4*>(act.h1) + r * 8;
+    const uint4* h2 = reinterpret_cast<const uint4*>(act.h2) + r * 8;
+    const uint4* a2 = reinterpret_cast<const uint4*>(act.da2) + r * 8;
+    const uint4* a1 = reinterpret_cast<const uint4*>(act.da1) + r * 8;
 #pragma unroll
-  for (int q = 0; q < 2; ++q) {   // dW1[ch = g][hidden n]; rows g + 8 are the zero padding
-    const int n = 16 * warp + 8 * q + 2 * t;
-    atomicAdd(grads + nn::P_W1 + g * 64 + n, w1acc[q][0]);
-    atomicAdd(grads + nn::P_W1 + g * 64 + n + 1, w1acc[q][1]);
+    for (int q = 0; q < 8; ++q) {
+      scatter_row(s.a1, 8 * q, tid, live ? h1[q] : z);
+      scatter_row(s.a1, 64 + 8 * q, tid, live ? h2[q] : z);
+      scatter_row(s.b, 8 * q, tid, live ? a1[q] : z);
+      scatter_row(s.b, 64 + 8 * q, tid, live ? a2[q] : z);
+    }
+    scatter_row(s.a2, 0, tid, live ? reinterpret_cast<const uint4*>(act.x)[r] : z);
+    scatter_row(s.b, 128, tid, live ? reinterpret_cast<const uint4*>(act.dy)[r] : z);
+    scatter_row(s.b, 136, tid, z);
+    asm volatile("fence.proxy.async.shared::cta;");
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    if (tid == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;");
+#pragma unroll
+      for (int kk = 0; kk < 8; ++kk) {
+        const uint32_t acc = (chunks_done > 0 || kk > 0) ? 1u : 0u;
+        // B rows 64..143 start at the 8th 8-row group (2048 bytes per group at K = 128)
+        tc::mma(d1, tc::desc(s.a1 + kk * 256, 128), tc::desc(s.b + 8 * 2048 + kk * 256, 128),
+                tc::idesc(128, 80), acc);
+        tc::mma(d2, tc::desc(s.a2 + kk * 256, 128), tc::desc(s.b + kk * 256, 128), tc::idesc(128, 144), acc);
+      }
+      tc::commit(&s.bar);
+      if (!tc::wait_bar(&s.bar, parity)) s.abort = 1;   // the tiles are restaged only after this
+    }
+    parity ^= 1;
+    ++chunks_done;
+    __syncthreads();
+    if (s.abort) break;
   }
-  for (int q = 0; q < 2; ++q) {
-    const int k = threadIdx.x + 128 * q;
-    if (k >= nn::NBIAS) break;
-    if (k < 64) atomicAdd(grads + nn::P_B1 + k, bsum[q]);
-    else if (k < 128) atomicAdd(grads + nn::P_B2 + (k - 64), bsum[q]);
-    else if (k - 128 < 7) atomicAdd(grads + nn::P_B3 + (k - 128), bsum[q]);
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  if (chunks_done > 0 && !s.abort) {
+    const uint32_t lane_off = (uint32_t)(32 * warp) << 16;
+    const int m = tid;                      // accumulator row = thread
+    uint32_t v[32];
+    // D1 columns 0..63: dW2 (rows < 64); columns 64..79: dW3 (rows >= 64)
+#pragma unroll
+    for (int cb = 0; cb < 2; ++cb) {
+      tc::tmem_ld<32>(d1 + lane_off + 32 * cb, v);
+      if (m < 64)
+        for (int n = 0; n < 32; ++n) atomicAdd(grads + nn::P_W2 + m * 64 + 32 * cb + n, __uint_as_float(v[n]));
+    }
+#pragma unroll
+    for (int cb = 0; cb < 2; ++cb) {
+      tc::tmem_ld<8>(d1 + lane_off + 64 + 8 * cb, v);
+      if (m >= 64)
+        for (int o = 0; o < 8 && 8 * cb + o < 7; ++o)
+          atomicAdd(grads + nn::P_W3 + (m - 64) * 7 + 8 * cb + o, __uint_as_float(v[o]));
+    }
+    // D2 columns 0..63: dW1 (rows < 8), db1 (row 8); 64..127: db2 (row 8); 128..134: db3
+#pragma unroll
+    for (int cb = 0; cb < 4; ++cb) {
+      tc::tmem_ld<32>(d2 + lane_off + 32 * cb, v);
+      for (int n = 0; n < 32; ++n) {
+        const int col = 32 * cb + n;
+        if (m < 8 && col < 64) atomicAdd(grads + nn::P_W1 + m * 64 + col, __uint_as_float(v[n]));
+        if (m == 8) atomicAdd(grads + (col < 64 ? nn::P_B1 + col : nn::P_B2 + col - 64), __uint_as_float(v[n]));
+      }
+    }
+    tc::tmem_ld<8>(d2 + lane_off + 128, v);
+    if (m == 8)
+      for (int o = 0; o < 7; ++o) atomicAdd(grads + nn::P_B3 + o, __uint_as_float(v[o]));
   }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  if (tid == 0 && s.abort) atomicOr(status, STF_DEV_MMA_TIMEOUT);
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(s.tmem), "n"(tcw::TMEM_COLS));
+}
+
+static cudaError_t launch_wgrad_tc(const ActBuffers& act, int64_t batch, float* grads, unsigned* status,
+                                   cudaStream_t s) {
+  const int smem = (int)sizeof(tcw::Smem) + 1024;
+  static bool attr = false;
+  if (!attr) {
+    const cudaError_t e = cudaFuncSetAttribute(k_neural_wgrad_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  int sms = 0, dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int64_t nchunks = (batch + 127) / 128;
+  // a few chunks per CTA, so that the accumulators' atomic flush is amortised
+  const int64_t want = (nchunks + 3) / 4;
+  const int grid = (int)(want < (int64_t)sms ? (want < 1 ? 1 : want) : (int64_t)sms);
+  k_neural_wgrad_tc<<<grid, 128, smem, s>>>(act, batch, grads, status);
+  return cudaGetLastError();
+}
+
+// Launch of the tcgen05 forward and backward over a batch.
+static cudaError_t launch_fwd_bwd_tc(const NeuralDev& nd, const TrainArgs& ta, const ActBuffers& act,
+                                     cudaStream_t s) {
+  const int smem = (int)sizeof(tct::Smem) + 1024;
+  static bool attr = false;
+  if (!attr) {
+    const cudaError_t e = cudaFuncSetAttribute(k_neural_fwd_bwd_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  int sms = 0, dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int64_t ntiles = (ta.batch + 127) / 128;
+  const int grid = (int)(ntiles < (int64_t)sms * 2 ? ntiles : (int64_t)sms * 2);
+  k_neural_fwd_bwd_tc<<<grid, 128, smem, s>>>(nd, ta, act);
+  return cudaGetLastError();
 }
 
 // Binary16 weight images and padded biases from the float32 parameters.
@@ -1072,7 +1239,22 @@ static cudaError_t run_neural(Op op, const NeuralDev& nd, const LookupArgs& a, c
     k_neural_stochastic_tc<F><<<grid, 256, smem, s>>>(nd, a);
     return cudaGetLastError();
   }
-  else if (op == OP_DETERMINISTIC) k_neural_deterministic<F><<<blocks, 128, 0, s>>>(nd, a);
+  else if (op == OP_DETERMINISTIC) {
+    const int smem = (int)sizeof(tcd::Smem) + 1024;
+    static bool attr_d = false;
+    if (!attr_d) {
+      cudaFuncSetAttribute(k_neural_deterministic_tc<F>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+      attr_d = true;
+    }
+    int sms = 0, dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int parts = (a.lod != nullptr && nd.nlev > 1 && a.level_mode != STF_LEVEL_NEAREST) ? 2 : 1;
+    const int q = 128 / (parts * Filter<F>::T * Filter<F>::T);
+    const int64_t ntiles = (a.n + q - 1) / q;
+    const int grid = (int)(ntiles < (int64_t)sms * 6 ? ntiles : (int64_t)sms * 6);
+    k_neural_deterministic_tc<F><<<grid, 128, smem, s>>>(nd, a);
+  }
   else return cudaErrorNotSupported;
   return cudaGetLastError();
 }
@@ -1192,11 +1374,6 @@ static cudaError_t alloc_acts(ActBuffers& act, void** block, int64_t batch) {
   return cudaSuccess;
 }
 
-static int train_blocks(int64_t rows, int per_block) {
-  const int64_t need = (rows + per_block - 1) / per_block;
-  const int64_t cap = (int64_t)grid_blocks(1LL << 40, 128);
-  return (int)(need < cap ? (need < 1 ? 1 : need) : cap);
-}
 
 static stf_status neural_handle(stf_texture t) {
   if (!handle_ok(t)) return fail(STF_ERR_INVALID_HANDLE, "unknown texture handle");
@@ -1230,9 +1407,8 @@ extern "C" stf_status stf_neural_gradients(stf_texture t, const int64_t* ids, in
   e = cudaMemsetAsync(t->n_grads, 0, sizeof(float) * nn::NPARAM, s);
   if (e == cudaSuccess) e = cudaMemsetAsync(t->n_loss, 0, sizeof(float), s);
   if (e == cudaSuccess) {
-    k_neural_fwd_bwd<<<train_blocks(batch, 128), 128, 0, s>>>(t->neural, ta, act);
-    k_neural_wgrad<<<train_blocks(batch, 64), 128, 0, s>>>(act, batch, t->n_grads);
-    e = cudaGetLastError();
+    e = launch_fwd_bwd_tc(t->neural, ta, act, s);
+    if (e == cudaSuccess) e = launch_wgrad_tc(act, batch, t->n_grads, t->d_status, s);
   }
   if (e == cudaSuccess && d_param_grads)
     e = cudaMemcpyAsync(d_param_grads, t->n_grads, sizeof(float) * nn::NPARAM, cudaMemcpyDeviceToDevice, s);
@@ -1276,8 +1452,9 @@ extern "C" stf_status stf_neural_train(stf_texture t, const float* d_target, con
     e = cudaMemsetAsync(t->n_grads, 0, sizeof(float) * nn::NPARAM, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(t->n_loss, 0, sizeof(float), s);
     if (e != cudaSuccess) break;
-    k_neural_fwd_bwd<<<train_blocks(cfg->batch, 128), 128, 0, s>>>(t->neural, ta, act);
-    k_neural_wgrad<<<train_blocks(cfg->batch, 64), 128, 0, s>>>(act, cfg->batch, t->n_grads);
+    e = launch_fwd_bwd_tc(t->neural, ta, act, s);
+    if (e == cudaSuccess) e = launch_wgrad_tc(act, cfg->batch, t->n_grads, t->d_status, s);
+    if (e != cudaSuccess) break;
     k_neural_adam<<<1, 256, 0, s>>>(t->n_params, t->n_m, t->n_v, t->n_grads, (float)(t->n_step + 1),
                                     cfg->lr_params, cfg->beta1, cfg->beta2, cfg->eps,
                                     (__half*)t->neural.wimg, (float*)t->neural.bias, t->n_loss,

@@ -169,6 +169,18 @@ stf_status build_sparse(stf_texture_s* t, const stf_texture_desc* d, cudaStream_
   t->bytes += (int64_t)total;
   char* p = (char*)t->d_tree;
   SparseDev& g = t->sparse;
+  // bounding box of the active leaves, clamped to +-2^30 (coordinates beyond 2^24 are
+  // clamped by the lookups, so the clamp changes no answer)
+  for (int a = 0; a < 3; ++a) {
+    int64_t lo = INT64_MAX, hi = INT64_MIN;
+    for (int64_t l = 0; l < nl; ++l) {
+      lo = std::min<int64_t>(lo, org[3 * l + a]);
+      hi = std::max<int64_t>(hi, (int64_t)org[3 * l + a] + 8);
+    }
+    if (nl == 0) lo = hi = 0;
+    g.bb_lo[a] = (int32_t)std::max<int64_t>(std::min<int64_t>(lo, 1 << 30), -(1 << 30));
+    g.bb_hi[a] = (int32_t)std::max<int64_t>(std::min<int64_t>(hi, 1 << 30), -(1 << 30));
+  }
   g.n_upper = n_upper;
   g.n_lower = n_lower;
   g.n_leaves = nl;
@@ -298,13 +310,20 @@ __device__ __forceinline__ void stage_upper(const SparseDev& g, UpperSmem& su) {
 
 // One stochastic lookup at coordinates x (caller's query index j).  J is int64_t, or
 // uint32_t in the fast loops.
+// With a miss box (the fast loops, which write no tap output), a fixed-window filter
+// whose window lies outside the active leaves' bounding box returns the background
+// without drawing.
 template <int F, int FMT, bool REUSE, typename J>
 __device__ __forceinline__ float sparse_stochastic_at(const SparseDev& g, const UpperSmem& su,
                                                       const LookupArgs& a, float* x, J j,
-                                                      uint32_t sample, int4& tap) {
+                                                      uint32_t sample, int4& tap,
+                                                      const MissBox* miss = nullptr) {
   if (!prepare_coords<3>(x)) {
     tap = make_int4(0, 0, 0, -1);
     return g.background;
+  }
+  if constexpr (FixedWindow<F>::value) {
+    if (miss && misses(*miss, x)) return g.background;
   }
   const uint4 r = query_variates(a, j, sample);
   if constexpr (IsFis<F>::value) {
@@ -348,19 +367,21 @@ template <int F, int FMT, bool REUSE>
 __global__ void __launch_bounds__(256) k_sparse_stochastic(SparseDev g, LookupArgs a) {
   __shared__ UpperSmem su;
   stage_upper(g, su);
+  const MissBox mb = miss_box<F>(g.bb_lo[0], g.bb_lo[1], g.bb_lo[2], g.bb_hi[0], g.bb_hi[1], g.bb_hi[2]);
   if (quad_loop3_ok(a)) {
     quad_loop3(a, [&](float x0, float x1, float x2, uint32_t j) {
       float x[3] = {x0, x1, x2};
       int4 tap;
-      return sparse_stochastic_at<F, FMT, REUSE>(g, su, a, x, j, a.sample_index, tap);
+      return sparse_stochastic_at<F, FMT, REUSE>(g, su, a, x, j, a.sample_index, tap, &mb);
     });
     return;
   }
   if (fast_loop(a)) {
     const uint32_t n = (uint32_t)a.n, stride = gridDim.x * blockDim.x;
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+      float x[3] = {__ldg(a.coords + 3 * i), __ldg(a.coords + 3 * i + 1), __ldg(a.coords + 3 * i + 2)};
       int4 tap;
-      a.out[i] = sparse_stochastic_one<F, FMT, REUSE>(g, su, a, i, i, a.sample_index, tap);
+      a.out[i] = sparse_stochastic_at<F, FMT, REUSE>(g, su, a, x, i, a.sample_index, tap, &mb);
     }
     return;
   }
@@ -398,6 +419,13 @@ __global__ void __launch_bounds__(256) k_sparse_deterministic(SparseDev g, Looku
       Fl::weights(fx, wx);
       Fl::weights(fy, wy);
       Fl::weights(fz, wz);
+      // a window outside the active leaves' bounding box on some axis reads only the
+      // background, and the weights sum to one (partition of unity)
+      if (bx + Fl::T <= g.bb_lo[0] || by + Fl::T <= g.bb_lo[1] || bz + Fl::T <= g.bb_lo[2] ||
+          bx >= g.bb_hi[0] || by >= g.bb_hi[1] || bz >= g.bb_hi[2]) {
+        a.out[i] = g.background;
+        continue;
+      }
       const int lx[2] = {bx >> 3, (bx + Fl::T - 1) >> 3};
       const int ly[2] = {by >> 3, (by + Fl::T - 1) >> 3};
       const int lz[2] = {bz >> 3, (bz + Fl::T - 1) >> 3};

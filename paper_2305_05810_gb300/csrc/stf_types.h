@@ -32,6 +32,9 @@ struct SparseDev {
   const float* leaf_scale;         // E4M3 format: one scale per leaf
   float background;
   unsigned* status;
+  // Bounding box [bb_lo, bb_hi) of the active leaves in voxels (clamped to +-2^30;
+  // empty for a grid without leaves): outside it every voxel reads the background.
+  int32_t bb_lo[3], bb_hi[3];
 };
 
 // Device view of a neural texture (stf_neural.cu).

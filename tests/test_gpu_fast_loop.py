@@ -92,7 +92,11 @@ def test_sparse_fast_loop_equals_general_loop(filt, fmt):
     T = stf.Texture(stf.KIND_SPARSE3D, values, fmt=fmt, leaf_origins=origins)
     o = origins[np.arange(60000) % len(origins)].astype(np.float32)
     q = (o + synth.uniform(3 * 60000, 10).reshape(-1, 3) * np.float32(10) - np.float32(1)).astype(np.float32)
-    _same(T, to_dev(np.concatenate([q, _edge(3)])), **_params(filt))
+    # points around the active leaves' bounding box, inside and outside it (outside it the
+    # fast loop returns the background without drawing)
+    lo, hi = origins.min(axis=0), origins.max(axis=0) + 8
+    far = (lo + (synth.uniform(3 * 20000, 11).reshape(-1, 3) * 1.6 - 0.3) * (hi - lo)).astype(np.float32)
+    _same(T, to_dev(np.concatenate([q, far, _edge(3)])), **_params(filt))
 
 
 @pytest.mark.parametrize("C", [1, 2, 4])
