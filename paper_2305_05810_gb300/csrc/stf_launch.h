@@ -11,11 +11,12 @@ enum Op { OP_STOCHASTIC = 0, OP_DETERMINISTIC = 1, OP_ACCUMULATE = 2 };
 // Grid size for a grid-stride launch: enough blocks for n, capped at `waves` full waves
 // of 2048 threads per SM.
 int grid_blocks(int64_t n, int threads, int waves = 4);
-// The stochastic dense and sparse kernels launch up to 16 waves: 16 waves of shorter
-// blocks finished the dense kernel 3% and the sparse kernel 4% sooner than 4 waves of
-// longer ones (the last wave leaves fewer SMs idle); one block per 256 queries was 20%
-// slower.  The 2D kernels keep 4 waves (no gain at 16.8M queries, 3% slower at 5.3M).
-constexpr int kStochasticWaves = 16;
+// The stochastic dense and sparse kernels launch up to 8 waves of 256-thread blocks.
+// With four queries per thread and the miss shortcut, 8 waves finished the dense
+// benchmark call 3% sooner than 16 and 6% sooner than 32 (2: 11% later; 4 and 6 within
+// 1% of 8, sparse 1-5% slower).  The 2D kernels keep 4 waves (no gain at 16.8M queries,
+// 3% slower at 5.3M with 16).
+constexpr int kStochasticWaves = 8;
 
 cudaError_t launch_tex2d(Op op, int filter, int fmt, int channels, const Tex2DView& t,
                          const LookupArgs& a, cudaStream_t s);
