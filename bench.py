@@ -123,6 +123,7 @@ def make_texture(stf, w, fmt=None, train_steps=400):
         target = torch.from_numpy(np.concatenate([p.reshape(-1, 7) for p in pyr[:w["nlat"]]])).cuda()
         losses = T.train(target, steps=train_steps, batch=1 << 16, lr_latent=3e-2, lr_params=3e-3, seed=11)
         w["train_loss"] = (float(losses[0].item()), float(losses[-1].item())) if train_steps else None
+        w["train_steps"] = train_steps
         del target
         return T
     if w["name"] == "dense":
@@ -353,6 +354,11 @@ def _oracle_chunk(job):
     if name == "neural":
         filters.lookup_2d(ref, q, lod, filt, stochastic_form=True, seed=1, qid=qid,
                           level_mode=filters.LEVEL_NEAREST)
+    elif name == "aniso":                   # lod carries the uv derivatives; filt the anisotropy
+        from oracle import ewa
+        ewa.lookup(ref, q, lod, filt, stochastic_form=True, seed=1, qid=qid)
+    elif name == "dct":
+        filters.lookup_2d(ref, q, lod, filt, stochastic_form=True, seed=1, qid=qid)
     elif name != "tex2d":
         filters.lookup_3d(ref, q, filt, stochastic_form=True, seed=1, qid=qid)
     else:
@@ -400,6 +406,24 @@ class OraclePool:
         self.pool.join()
 
 
+def pooled_oracle_rate(ref, name, filt, q, aux, chunk):
+    """Oracle lookups/s over q (with aux: lod or derivatives) on every host core, one
+    spawned process per core holding ref; returns (rate, seconds, cores)."""
+    import multiprocessing as mp
+    cores = os.cpu_count() or 1
+    pool = mp.get_context("spawn").Pool(cores, initializer=_oracle_init, initargs=(ref, name, filt))
+    try:
+        pool.map(_oracle_chunk, [(0, q[:64], aux[:64])] * (4 * cores), chunksize=1)
+        jobs = [(a, q[a:a + chunk], aux[a:a + chunk]) for a in range(0, q.shape[0], chunk)]
+        t0 = time.perf_counter()
+        done = sum(pool.map(_oracle_chunk, jobs, chunksize=1))
+        dt = time.perf_counter() - t0
+    finally:
+        pool.close()
+        pool.join()
+    return done / dt, dt, cores
+
+
 def cpu_oracle_rate(w, filt, n_queries):
     """Oracle lookups/s on the first n_queries queries (stochastic) on every host core;
     returns (rate, seconds, cores)."""
@@ -415,11 +439,13 @@ def storage_error(stf, torch, w, tex, filt, stream, m=1 << 17, level_mode=None):
     """Error of the library's stochastic and deterministic lookups on the stored
     texture (FP16 / E4M3 + leaf scale / FP32; the neural texture's FP16 latents and
     decoder) against the float64 oracle on the unquantised texels (the float32 values
-    the texture was built from; for the neural texture, the target it was trained on),
-    over m consecutive queries from the middle of the workload.  The stochastic pair
-    draws the same taps (queries whose tap the oracle marks exempt are left out), so
-    its error is the storage error of the fetched texel; the deterministic pair
-    compares the full filters.  Oracle leg only: part of the CPU-baseline run."""
+    the texture was built from; for the neural texture, its float32 master latents and
+    weights, and beside that the target texture it was trained on, which measures the
+    fit of the network rather than its storage), over m consecutive queries from the
+    middle of the workload.  The stochastic pair draws the same taps (queries whose
+    tap the oracle marks exempt are left out), so its error is the storage error of
+    the fetched texel; the deterministic pair compares the full filters.  Oracle leg
+    only: part of the CPU-baseline run."""
     from oracle import filters, textures
     n = w["coords"].shape[0]
     m = min(m, n)
@@ -447,17 +473,27 @@ def storage_error(stf, torch, w, tex, filt, stream, m=1 << 17, level_mode=None):
         sub = touched_leaves(w["origins"], q)
         ref = textures.Sparse3D(w["origins"][sub], np.asarray(w["values"][sub], dtype=np.float64))
     elif w["name"] == "neural":
-        ref = textures.Texture2D([np.asarray(p_, dtype=np.float64) for p_ in w["pyramid"]])
+        from oracle import mlp, neural
+        lat, o, levels = np.asarray(w["trained_latents"], dtype=np.float64), 0, []
+        for L in range(w["nlat"]):
+            s_ = max(1, w["size"] >> L)
+            levels.append(lat[o:o + s_ * s_].reshape(s_, s_, 8))
+            o += s_ * s_
+        ref = neural.NeuralTexture2D(levels, mlp.unflatten(np.asarray(w["trained_params"], dtype=np.float64)),
+                                     [np.asarray(p_, dtype=np.float64) for p_ in w["pyramid"][w["nlat"]:]])
     else:
         ref = textures.Texture2D([np.asarray(w["values"], dtype=np.float64)])
-    if ref.__class__.__name__ == "Texture2D":
-        rv, rt, ex = filters.lookup_2d(ref, q, lod, filt, stochastic_form=True, level_mode=lm, qid=qid,
-                                       seed=2024)
-        dv, _, _ = filters.lookup_2d(ref, q, lod, filt, stochastic_form=False, level_mode=lm)
-    else:
-        rv, rt, ex = filters.lookup_3d(ref, q, filt, stochastic_form=True, qid=qid, seed=2024)
-        dv, _, _ = filters.lookup_3d(ref, q, filt, stochastic_form=False)
-    same = np.all(taps == rt, axis=1) & ~ex
+
+    def oracle(ref):
+        if ref.__class__.__name__ in ("Texture2D", "NeuralTexture2D"):
+            rv, rt, ex = filters.lookup_2d(ref, q, lod, filt, stochastic_form=True, level_mode=lm, qid=qid,
+                                           seed=2024)
+            dv, _, _ = filters.lookup_2d(ref, q, lod, filt, stochastic_form=False, level_mode=lm)
+        else:
+            rv, rt, ex = filters.lookup_3d(ref, q, filt, stochastic_form=True, qid=qid, seed=2024)
+            dv, _, _ = filters.lookup_3d(ref, q, filt, stochastic_form=False)
+        return rv, rt, ex, dv
+
     vals = np.asarray(w["pyramid"][0] if w["name"] == "neural" else w["values"], dtype=np.float64)
     rng = float(vals.max() - vals.min())
 
@@ -465,10 +501,22 @@ def storage_error(stf, torch, w, tex, filt, stream, m=1 << 17, level_mode=None):
         e = np.abs(e)
         return {"max_abs": float(e.max()), "rms": float(np.sqrt(np.mean(e * e))),
                 "max_rel_to_range": float(e.max() / rng)}
-    return {"stochastic": stats(got[same] - rv[same]), "deterministic": stats(det - dv),
-            "queries": m, "same_taps": int(same.sum()), "value_range": rng,
-            "against": "float64 oracle on the unquantised texels" if w["name"] != "neural"
-                       else "float64 oracle on the target texture the network was trained on"}
+
+    def compare(ref):
+        rv, rt, ex, dv = oracle(ref)
+        same = np.all(taps == rt, axis=1) & ~ex
+        return {"stochastic": stats(got[same] - rv[same]), "deterministic": stats(det - dv),
+                "same_taps": int(same.sum())}
+
+    out = compare(ref)
+    out.update(queries=m, value_range=rng, against="float64 oracle on the unquantised texels"
+               if w["name"] != "neural" else "float64 oracle on the float32 master latents and weights")
+    if w["name"] == "neural":
+        fit = compare(textures.Texture2D([np.asarray(p_, dtype=np.float64) for p_ in w["pyramid"]]))
+        fit["against"] = "float64 oracle on the target texture the network was trained on"
+        fit["train_steps"] = w.get("train_steps")
+        out["fit_to_target"] = fit
+    return out
 
 
 # ------------------------------------------------------------------ arms
@@ -636,12 +684,11 @@ def run_aniso(args):
     if not args.no_cpu_baseline:
         from oracle import ewa, textures
         ref = textures.Texture2D.box_pyramid(base.astype(np.float64), levels)
-        m = 2000
-        t0 = time.perf_counter()
-        ewa.lookup(ref, uv_h[:m], g_h[:m], ma, stochastic_form=True, seed=2024)
-        dt = time.perf_counter() - t0
-        line["cpu_baseline"] = {"value": m / dt, "unit": "lookups/s", "cores": 1, "kind": "oracle",
-                                "sample": "first %d queries, stochastic EWA" % m}
+        m = min(n, 1 << 16)
+        rate, dt, cores = pooled_oracle_rate(ref, "aniso", ma, uv_h[:m], g_h[:m], 1024)
+        line["cpu_baseline"] = {"value": rate, "unit": "lookups/s", "cores": cores, "kind": "oracle",
+                                "sample": "first %d queries, stochastic EWA, %.1f s on %d processes"
+                                          % (m, dt, cores)}
     print(json.dumps(line), flush=True)
     tex.close()
     return 0
@@ -745,18 +792,16 @@ def run_dct(args):
     }
     if not args.no_cpu_baseline:
         # the oracle's float64 encoder on the same pyramid (set-up, untimed), then its
-        # stochastic trilinear lookups on the first 20,000 queries (timed)
+        # stochastic trilinear lookups on the first 2^22 queries (timed)
         from oracle import dct as odct
-        from oracle import filters
         lv = [p.astype(np.float64) for p in synth.box_levels(base, levels)]
         ref = odct.DCTTexture2D(lv)
-        m = 20000
-        lod_h = lod.cpu().numpy()
-        t0 = time.perf_counter()
-        filters.lookup_2d(ref, uv_h[:m], lod_h[:m], "linear", stochastic_form=True, seed=2024)
-        dt = time.perf_counter() - t0
-        line["cpu_baseline"] = {"value": m / dt, "unit": "lookups/s", "cores": 1, "kind": "oracle",
-                                "sample": "first %d queries, stochastic trilinear on the DCT texture" % m}
+        del lv
+        m = min(n, 1 << 22)
+        rate, dt, cores = pooled_oracle_rate(ref, "dct", "linear", uv_h[:m], lod.cpu().numpy()[:m], 1 << 16)
+        line["cpu_baseline"] = {"value": rate, "unit": "lookups/s", "cores": cores, "kind": "oracle",
+                                "sample": "first %d queries, stochastic trilinear on the DCT texture, "
+                                          "%.1f s on %d processes" % (m, dt, cores)}
     print(json.dumps(line), flush=True)
     tex.close()
     return 0
