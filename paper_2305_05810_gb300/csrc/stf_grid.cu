@@ -82,17 +82,35 @@ __device__ __forceinline__ float dense_stochastic_one(const Dense3DView& g, cons
   return dense_stochastic_at<F, FMT, REUSE, OFF32>(g, a, x, j, sample, tap);
 }
 
-// Six resident 256-thread blocks per SM (at most 40 registers a thread) for the one-tap
-// filters: 1.4% sooner than five on the dense benchmark call, without spills; the
-// two-tap positivized Catmull-Rom would spill at that cap and keeps the default.
+// Resident 256-thread blocks per SM: six (at most 40 registers a thread) for the tent
+// and B-spline filters, 1.4% sooner than five on the dense benchmark call without
+// spills; five for Catmull-Rom and the Gaussian, which would spill at 40; four for
+// the two-tap positivized Catmull-Rom (at 84 registers and three blocks it ran 17%
+// slower).
 template <int F>
-constexpr int dense_stochastic_min_blocks() { return F == STF_FILTER_CATMULL_ROM_POSITIVIZED ? 1 : 6; }
+constexpr int dense_stochastic_min_blocks() {
+  return F == STF_FILTER_CATMULL_ROM_POSITIVIZED ? 4
+         : (F == STF_FILTER_CATMULL_ROM || F == STF_FILTER_FIS_GAUSSIAN) ? 5 : 6;
+}
 
 template <int F, int FMT, bool REUSE>
 __global__ void __launch_bounds__(256, dense_stochastic_min_blocks<F>()) k_dense_stochastic(Dense3DView g,
                                                                                          LookupArgs a) {
   const bool off32 = (uint64_t)g.nx * (uint64_t)g.ny * (uint64_t)g.nz <= (uint64_t(1) << 32);
   const MissBox mb = miss_box<F>(0, 0, 0, g.nx, g.ny, g.nz);
+  if constexpr (JointOneTap<F, REUSE>::value) {
+    if (off32 && quad_loop3_ok(a)) {
+      quad_loop3_joint(a, [&](float (&x)[4][3], uint32_t i) {
+        return joint_one_tap4<F>(a, x, i, mb, g.background,
+                                 [&](const int* t) { return dense_fetch<FMT, true>(g, t[0], t[1], t[2]); });
+      }, [&](float x0, float x1, float x2, uint32_t j) {
+        float x[3] = {x0, x1, x2};
+        int4 tap;
+        return dense_stochastic_at<F, FMT, REUSE, true>(g, a, x, j, a.sample_index, tap, &mb);
+      });
+      return;
+    }
+  }
   if (off32 && quad_loop3_ok(a)) {
     quad_loop3(a, [&](float x0, float x1, float x2, uint32_t j) {
       float x[3] = {x0, x1, x2};
