@@ -527,15 +527,16 @@ struct DetRow {
 
 template <int F>
 __device__ __forceinline__ DetRow det_row(const NeuralDev& nd, const LookupArgs& a, int64_t i, int p, int tx,
-                                          int ty, uint4* arow) {
+                                          int ty, uint4* arow, const QueryCoords* pre = nullptr) {
   using Fl = Filter<F>;
   DetRow d;
   d.i = i;
   d.w = 0.0f;
   d.mode = 0;
   if (i >= a.n) return d;
-  const float2 uv = reinterpret_cast<const float2*>(a.coords)[i];
-  const float lod = a.lod ? a.lod[i] : 0.0f;
+  const QueryCoords qc = pre ? *pre : load_coords(a, i);
+  const float2 uv = qc.uv;
+  const float lod = qc.lod;
   if (!(isfinite(lod) && isfinite(uv.x) && isfinite(uv.y))) return d;
   float lw = p == 0 ? 1.0f : 0.0f;
   int L = 0;
@@ -623,6 +624,7 @@ __global__ void __launch_bounds__(128, 6) k_neural_deterministic_tc(NeuralDev nd
   DetRow cur;
   if (tile < ntiles) cur = det_row<F>(nd, a, tile * Q + qi, p, tx, ty, arow);
   cp_async_commit();
+  QueryCoords qn = load_coords(a, (tile + gridDim.x) * Q + qi);   // a tile ahead
   for (; tile < ntiles; tile += gridDim.x) {
     cp_async_wait<0>();
     uint4 fb = make_uint4(0, 0, 0, 0);
@@ -632,8 +634,9 @@ __global__ void __launch_bounds__(128, 6) k_neural_deterministic_tc(NeuralDev nd
     // A1 is free: gather the next tile's texels while this tile's layers run
     const int64_t next = tile + gridDim.x;
     DetRow nxt;
-    if (next < ntiles) nxt = det_row<F>(nd, a, next * Q + qi, p, tx, ty, arow);
+    if (next < ntiles) nxt = det_row<F>(nd, a, next * Q + qi, p, tx, ty, arow, &qn);
     cp_async_commit();
+    qn = load_coords(a, (next + gridDim.x) * Q + qi);
     tc_hidden(trow, s.a2, tid);
     if (!run([&] {
           for (int kk = 0; kk < 4; ++kk)
