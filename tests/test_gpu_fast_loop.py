@@ -85,6 +85,42 @@ def test_dense_fast_loop_equals_general_loop(filt, fmt):
     _same(T, to_dev(np.concatenate([q, _edge(3)])), **_params(filt))
 
 
+def _miss_box_edges(n):
+    """Coordinates on and next to the boundaries of the miss test of a grid of n voxels per
+    axis (the tent's window misses for x < -1 or x >= n, the B-spline's for x < -2 or
+    x >= n + 1), one axis at a time, the others inside the grid."""
+    vals = []
+    for b in (-2.0, -1.0, float(n), float(n + 1)):
+        vals += [np.nextafter(np.float32(b), np.float32(-np.inf)), np.float32(b),
+                 np.nextafter(np.float32(b), np.float32(np.inf))]
+    rows = []
+    for a in range(3):
+        for v in vals:
+            r = [np.float32(n / 2 + 0.25)] * 3
+            r[a] = v
+            rows.append(r)
+    return np.array(rows, dtype=np.float32)
+
+
+@pytest.mark.parametrize("fmt", [stf.FMT_F32, stf.FMT_F16])
+@pytest.mark.parametrize("filt", FILTERS)
+def test_dense_quads_mixing_live_and_dead_queries(filt, fmt):
+    """Four-query groups in which some queries are dead (NaN, infinite, huge, or with a
+    window outside the grid) and others live: the joint form draws for all four and
+    keeps only the live results, so every query must equal the general loop's; queries
+    on the miss test's boundaries check that the shortcut is exact."""
+    n = 40
+    vals = synth.dense_density(n=n, seed=6, period=9.0)
+    T = stf.Texture(stf.KIND_DENSE3D, vals, dims=(n, n, n), fmt=fmt)
+    q = (synth.uniform(3 * 40003, 12).reshape(-1, 3) * np.float32(48) - np.float32(4)).astype(np.float32)
+    special = np.concatenate([_edge(3), _miss_box_edges(n)])
+    rng = np.random.default_rng(5)
+    pos = rng.choice(q.shape[0], size=4000, replace=False)
+    q[pos] = special[rng.integers(0, special.shape[0], size=pos.size)]
+    q[: special.shape[0]] = special                     # and a run of them at the start
+    _same(T, to_dev(q), **_params(filt))
+
+
 @pytest.mark.parametrize("fmt", [stf.FMT_F32, stf.FMT_E4M3_SCALED])
 @pytest.mark.parametrize("filt", FILTERS)
 def test_sparse_fast_loop_equals_general_loop(filt, fmt):

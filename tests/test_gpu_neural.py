@@ -204,3 +204,28 @@ def test_full_size_neural_sampled():
         bound[m] = decode_bound(Z, ref.P)
     err = np.abs(g_out - rv)
     assert np.all(err[same] <= bound[same] + 2e-6 * np.abs(rv[same])), np.max(err[same] - bound[same])
+
+    # the benchmark's call asks for no tap output (the slim decode): the same outputs, every query
+    slim = T.lookup(to_dev(uv), to_dev(lod), filter="linear", seed=2024, level_mode=stf.LEVEL_NEAREST)
+    torch.cuda.synchronize()
+    torch.testing.assert_close(slim, out, rtol=0, atol=0)
+
+
+@pytest.mark.parametrize("level_mode", [stf.LEVEL_NEAREST, stf.LEVEL_STOCHASTIC])
+@pytest.mark.parametrize("filt", ["linear", "bspline3", "catmull_rom"])
+def test_neural_slim_decode_equals_tap_output_decode(filt, level_mode):
+    """Calls without tap output or permutation take the slim decode (several tiles per
+    group of threads); each query's output must equal the tap-output decode's bit for bit,
+    on an odd number of tiles with a ragged last one and NaN / infinite coordinates."""
+    T, _, _, _, _ = make_neural()
+    n = 128 * 37 + 51
+    uv = synth.uv_queries(n, seed=13)
+    lod = (synth.uniform(n, 14) * np.float32(7.0) - np.float32(0.5)).astype(np.float32)
+    uv[5] = [np.nan, 0.5]
+    uv[700] = [np.inf, 0.25]
+    lod[900] = np.nan
+    taps = torch.empty((n, 4), dtype=torch.int32, device=dev())
+    ref = T.lookup(to_dev(uv), to_dev(lod), taps=taps, filter=filt, seed=8, level_mode=level_mode)
+    slim = T.lookup(to_dev(uv), to_dev(lod), filter=filt, seed=8, level_mode=level_mode)
+    torch.cuda.synchronize()
+    torch.testing.assert_close(slim, ref, rtol=0, atol=0, equal_nan=True)
