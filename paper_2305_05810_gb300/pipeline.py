@@ -14,11 +14,16 @@ import paper_2305_05810_gb300 as stf
 
 
 class HostPipeline:
-    def __init__(self, texture, chunk=1 << 22, n_streams=3, device=None):
+    """tail: the last chunk's worth of queries is split into this many smaller chunks, so
+    that the lookup and device-to-host copy left after the final host-to-device copy
+    are short."""
+
+    def __init__(self, texture, chunk=1 << 22, n_streams=3, device=None, tail=1):
         import torch
         self.torch = torch
         self.tex = texture
         self.chunk = int(chunk)
+        self.tail = max(1, int(tail))
         self.device = device or torch.device("cuda", torch.cuda.current_device())
         self.streams = [torch.cuda.Stream(device=self.device) for _ in range(n_streams)]
         self.bufs = [{} for _ in range(n_streams)]
@@ -34,6 +39,16 @@ class HostPipeline:
             self.bufs[k][name] = b
         return b[:n].view(*shape)
 
+    def _chunks(self, n):
+        """[a, b) ranges covering 0..n: chunks of self.chunk, the last chunk's worth split
+        into self.tail pieces."""
+        edges = list(range(0, n, self.chunk)) + [n]
+        if self.tail > 1 and len(edges) > 2:
+            a = edges[-2]
+            step = -(-(n - a) // self.tail)
+            edges = edges[:-2] + list(range(a, n, step)) + [n]
+        return list(zip(edges[:-1], edges[1:]))
+
     def lookup(self, params, h_coords, h_out, h_lod=None, stochastic=True):
         """Filter every query of h_coords (n x 2 or n x 3, pinned) into h_out
         (n x channels, pinned) with the given stf_lookup_params."""
@@ -44,10 +59,9 @@ class HostPipeline:
         cur = torch.cuda.current_stream(self.device)
         for s in self.streams:
             s.wait_stream(cur)
-        for c, a in enumerate(range(0, n, self.chunk)):
+        for c, (a, b) in enumerate(self._chunks(n)):
             k = c % len(self.streams)
             s = self.streams[k]
-            b = min(n, a + self.chunk)
             m = b - a
             with torch.cuda.stream(s):
                 d_in = self._buf(k, "coords", (m, d), torch.float32)

@@ -85,9 +85,11 @@ def test_request_over_budget_is_rejected_on_gpu(textures):
         sched.submit(big)
 
 
-def test_host_pipeline_equals_one_device_call():
+@pytest.mark.parametrize("tail", [1, 5])
+def test_host_pipeline_equals_one_device_call(tail):
     """Chunked multi-stream lookups from pinned host memory return the results of one
-    device call over the whole batch (variates keyed by the global query index)."""
+    device call over the whole batch (variates keyed by the global query index), also
+    with the last chunk split into smaller ones."""
     from paper_2305_05810_gb300.pipeline import HostPipeline
     vals = synth.dense_density(n=64, seed=3, period=12.0)
     T = stf.Texture(stf.KIND_DENSE3D, vals, dims=(64, 64, 64), fmt=stf.FMT_F16)
@@ -96,7 +98,7 @@ def test_host_pipeline_equals_one_device_call():
     whole = T.lookup(torch.from_numpy(q).cuda(), filter="bspline3", seed=9, query_offset=123)
     h_q = torch.from_numpy(q).pin_memory()
     h_out = torch.empty((n, 1), dtype=torch.float32).pin_memory()
-    pipe = HostPipeline(T, chunk=10007, n_streams=3)
+    pipe = HostPipeline(T, chunk=10007, n_streams=3, tail=tail)
     pipe.lookup(stf.make_params("bspline3", seed=9, query_offset=123), h_q, h_out)
     torch.cuda.synchronize()
     assert torch.equal(whole.cpu(), h_out)
