@@ -82,6 +82,117 @@ __device__ __forceinline__ float dense_stochastic_one(const Dense3DView& g, cons
   return dense_stochastic_at<F, FMT, REUSE, OFF32>(g, a, x, j, sample, tap);
 }
 
+// Packed form of the four-query loop for the fixed-window filters (tent, B-spline, and
+// their FIS forms): a warp's 128 queries are tested against the miss box, each lane
+// writes the background over its four results, and the warp's live queries are then
+// packed onto its lanes, lane t taking the live queries of rank t, t + 32, ... in
+// (query-in-group, lane) order, R = ceil(live / 32) per lane, drawn, chosen and gathered
+// side by side.  A warp with at most 64 live queries thus runs one or two draws per lane
+// instead of four; a warp with more keeps each lane's own four (joint_one_tap4).  The
+// packed lanes reload their queries' coordinates (from L1: the warp has just read them)
+// and store each result over the background its owner wrote.
+// Position of the set bit of rank n (0-based) in m, for n < popc(m): a binary search on
+// the population counts of the low halves.
+__device__ __forceinline__ uint32_t nth_set_bit(uint32_t m, uint32_t n) {
+  uint32_t pos = 0;
+#pragma unroll
+  for (int w = 16; w >= 1; w >>= 1) {
+    const uint32_t low = __popc(m & ((1u << w) - 1u));
+    if (n >= low) {
+      n -= low;
+      m >>= w;
+      pos += (uint32_t)w;
+    }
+  }
+  return pos;
+}
+
+template <int F, int FMT, int R>
+__device__ __forceinline__ void dense_packed_rounds(const Dense3DView& g, const LookupArgs& a, uint32_t q0,
+                                                    const uint32_t (&b)[4], uint32_t live_count, uint32_t lane,
+                                                    uint32_t groups) {
+  const uint32_t c0 = __popc(b[0]), c1 = c0 + __popc(b[1]), c2 = c1 + __popc(b[2]);
+  uint32_t qi[R];
+  bool ok[R];
+  float x[R][3];
+#pragma unroll
+  for (int q = 0; q < R; ++q) {
+    const uint32_t r = lane + 32u * (uint32_t)q;
+    ok[q] = r < live_count;
+    const int k = r < c0 ? 0 : r < c1 ? 1 : r < c2 ? 2 : 3;
+    const uint32_t before = k == 0 ? 0u : k == 1 ? c0 : k == 2 ? c1 : c2;
+    const uint32_t bk = k == 0 ? b[0] : k == 1 ? b[1] : k == 2 ? b[2] : b[3];
+    const uint32_t src = ok[q] ? nth_set_bit(bk, r - before) : 0u;
+    qi[q] = 4u * (q0 + src) + (uint32_t)k;
+    ok[q] = ok[q] && qi[q] < 4u * groups;    // a live query lies in an active lane's group
+    x[q][0] = x[q][1] = x[q][2] = 0.0f;
+    if (ok[q]) {
+      x[q][0] = __ldg(a.coords + 3 * qi[q]);
+      x[q][1] = __ldg(a.coords + 3 * qi[q] + 1);
+      x[q][2] = __ldg(a.coords + 3 * qi[q] + 2);
+    }
+    prepare_coords<3>(x[q]);            // the owner's clamp of huge coordinates, again
+  }
+  uint4 rv[R];
+#pragma unroll
+  for (int q = 0; q < R; ++q) rv[q] = query_variates(a, qi[q], a.sample_index);
+  int t[R][3];
+#pragma unroll
+  for (int q = 0; q < R; ++q) draw_one_tap3<F>(a, x[q], qi[q], rv[q], t[q]);
+#pragma unroll
+  for (int q = 0; q < R; ++q)
+    if (ok[q]) a.out[qi[q]] = dense_fetch<FMT, true>(g, t[q][0], t[q][1], t[q][2]);
+}
+
+template <int F, int FMT>
+__device__ __forceinline__ void dense_packed_loop(const Dense3DView& g, const LookupArgs& a, const MissBox& mb) {
+  const uint32_t n = (uint32_t)a.n, groups = n >> 2, stride = gridDim.x * blockDim.x;
+  const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x, lane = threadIdx.x & 31u;
+  const float4* c4 = reinterpret_cast<const float4*>(a.coords);
+  float4* o4 = reinterpret_cast<float4*>(a.out);
+  const float bg = g.background;
+  // every lane of a warp runs the same iterations (the loop bound is the warp's first
+  // group), so the warp-wide votes below see all 32 lanes
+  for (uint32_t w0 = tid - lane; w0 < groups; w0 += stride) {
+    const uint32_t gq = w0 + lane;
+    const bool act = gq < groups;
+    float x[4][3] = {};
+    bool live[4] = {false, false, false, false};
+    if (act) {
+      const float4 p = __ldg(c4 + 3 * gq), q = __ldg(c4 + 3 * gq + 1), r = __ldg(c4 + 3 * gq + 2);
+      x[0][0] = p.x; x[0][1] = p.y; x[0][2] = p.z;
+      x[1][0] = p.w; x[1][1] = q.x; x[1][2] = q.y;
+      x[2][0] = q.z; x[2][1] = q.w; x[2][2] = r.x;
+      x[3][0] = r.y; x[3][1] = r.z; x[3][2] = r.w;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) live[k] = prepare_coords<3>(x[k]) && !misses(mb, x[k]);
+    }
+    uint32_t b[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) b[k] = __ballot_sync(0xffffffffu, live[k]);
+    const uint32_t live_count = __popc(b[0]) + __popc(b[1]) + __popc(b[2]) + __popc(b[3]);
+    // (every branch below is the same for all lanes)
+    if (live_count > 64) {
+      // mostly live: each lane its own four queries, side by side
+      if (act) o4[gq] = joint_one_tap4<F>(a, x, 4 * gq, mb, bg, [&](const int* t) {
+        return dense_fetch<FMT, true>(g, t[0], t[1], t[2]);
+      });
+      continue;
+    }
+    if (act) o4[gq] = make_float4(bg, bg, bg, bg);
+    if (live_count == 0) continue;
+    __syncwarp();                        // the owners' background stores come first
+    if (live_count <= 32) dense_packed_rounds<F, FMT, 1>(g, a, w0, b, live_count, lane, groups);
+    else dense_packed_rounds<F, FMT, 2>(g, a, w0, b, live_count, lane, groups);
+    __syncwarp();
+  }
+  for (uint32_t i = 4 * groups + tid; i < n; i += stride) {
+    float x[3] = {__ldg(a.coords + 3 * i), __ldg(a.coords + 3 * i + 1), __ldg(a.coords + 3 * i + 2)};
+    int4 tap;
+    a.out[i] = dense_stochastic_at<F, FMT, false, true>(g, a, x, i, a.sample_index, tap, &mb);
+  }
+}
+
 // Resident 256-thread blocks per SM: six (at most 40 registers a thread) for the tent
 // and B-spline filters, 1.4% sooner than five on the dense benchmark call without
 // spills; five for Catmull-Rom and the Gaussian, which would spill at 40; four for
@@ -98,6 +209,12 @@ __global__ void __launch_bounds__(256, dense_stochastic_min_blocks<F>()) k_dense
                                                                                          LookupArgs a) {
   const bool off32 = (uint64_t)g.nx * (uint64_t)g.ny * (uint64_t)g.nz <= (uint64_t(1) << 32);
   const MissBox mb = miss_box<F>(0, 0, 0, g.nx, g.ny, g.nz);
+  if constexpr (FixedWindow<F>::value && F != STF_FILTER_FIS_BSPLINE3 && !REUSE) {
+    if (off32 && quad_loop3_ok(a)) {
+      dense_packed_loop<F, FMT>(g, a, mb);
+      return;
+    }
+  }
   if constexpr (JointOneTap<F, REUSE>::value) {
     if (off32 && quad_loop3_ok(a)) {
       quad_loop3_joint(a, [&](float (&x)[4][3], uint32_t i) {
